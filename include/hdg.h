@@ -1,0 +1,197 @@
+/*
+ * hdg.h -- C ABI of the GB300 (sm_103a) statically condensed HDG library.
+ *
+ * The library solves the Helmholtz problem  lambda u - laplace u = f  with
+ * Dirichlet (u = g_D) or Neumann (n . grad u = g_N) data on the six sides of
+ * a Cartesian box (arXiv:2007.11891, Eq. (helmholtz_equation), Sec. 2.1),
+ * discretised by the hybridised LDG method (LDG-H) on cuboid elements with
+ * a tensor-product Lagrange basis on the Gauss-Lobatto-Legendre points of
+ * degree p (Sec. 2.2, Sec. 3.2) and the penalty tau_{i,e} = 2 tau_hat / h_{i,e}.
+ * After static condensation the unknowns are the traces u-tilde on the
+ * faces, and the global system is  K ut = F  (Eq. (hdg_system)).
+ *
+ * ---------------------------------------------------------------------------
+ * Data layout (all arrays are dense, little-endian, element/face-major)
+ * ---------------------------------------------------------------------------
+ *   n = p + 1 nodes per direction.  Elements (e1, e2, e3), 0 <= e_d < N_d,
+ *   have index e1 + N1 (e2 + N2 e3).
+ *
+ *   Volume vectors (f, u, gradients): n^3 values per element, node
+ *   i + n j + n^2 k (x1 fastest); hdg_volume_size() = n_e n^3 per
+ *   right-hand side.
+ *
+ *   Trace vectors: faces normal to direction d lie on grid planes 0..N_d.
+ *   A plane is an unknown unless it is the boundary plane of a Dirichlet
+ *   side; unknown planes of direction d are lo_d..hi_d with lo_d = 1 (0 if
+ *   the low side is Neumann) and hi_d = N_d - 1 (N_d if the high side is
+ *   Neumann).  The vector is the concatenation of the blocks d = 0, 1, 2;
+ *   block d holds its unknown planes in order, each with Na x Nb faces
+ *   (the other two element counts in increasing axis order, face a + Na b),
+ *   each face n x n nodes ordered by its two axes, lower axis fastest.
+ *   hdg_trace_size() values per right-hand side.
+ *
+ *   Boundary data vectors: the six sides 0..5 = (x1-, x1+, x2-, x2+, x3-,
+ *   x3+) in order, each with Na x Nb faces of n x n nodes as above; a
+ *   Dirichlet side holds nodal values of g_D, a Neumann side nodal values of
+ *   g_N = n . grad u (outer normal).  hdg_boundary_size() values.
+ *
+ *   Batches of nrhs right-hand sides are stored one after the other
+ *   (right-hand side r at offset r * size).
+ *
+ * ---------------------------------------------------------------------------
+ * Conventions
+ * ---------------------------------------------------------------------------
+ *   - Pointers named d_* are device pointers on the current CUDA device;
+ *     h_* are host pointers.  The caller owns every buffer it passes; the
+ *     context owns its tables and workspaces and frees them in hdg_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is enqueued on it; calls that return results
+ *     to the host (solve info) synchronise that stream.
+ *   - Every call returns an hdg_status and never aborts the process.  On an
+ *     error, hdg_last_error() returns a message for the calling thread.
+ *   - A context may be used by one host thread at a time.
+ */
+#ifndef HDG_GB300_H
+#define HDG_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdg_ctx hdg_ctx;
+
+typedef enum {
+  HDG_OK = 0,
+  HDG_ERR_INVALID_ARG = 1,   /* bad size, pointer, degree or option        */
+  HDG_ERR_SINGULAR = 2,      /* lambda = 0 and no Dirichlet side: K singular */
+  HDG_ERR_CUDA = 3,          /* a CUDA runtime call failed                  */
+  HDG_ERR_OOM = 4,           /* device allocation failed                    */
+  HDG_ERR_NOT_CONVERGED = 5, /* iteration limit reached before tolerance    */
+  HDG_ERR_BREAKDOWN = 6,     /* CG breakdown: p^T K p <= 0 or non-finite     */
+  HDG_ERR_UNSUPPORTED = 7    /* degree above 16, or not an sm_103 device    */
+} hdg_status;
+
+/* Precision of an operator application or of the inner CG solve.
+ *   HDG_FP64: FP64 storage and arithmetic.
+ *   HDG_FP32: FP32 storage and arithmetic.
+ *   HDG_BF16: BF16 storage of trace vectors, FP32 arithmetic.            */
+typedef enum { HDG_FP64 = 0, HDG_FP32 = 1, HDG_BF16 = 2 } hdg_precision;
+
+/* Basis of trace vectors.
+ *   HDG_BASIS_NODAL: nodal values on the GLL points (the K of Eq. (hdg_system),
+ *     evaluated as in Alg. (hdg_op_3d)).
+ *   HDG_BASIS_TRANSFORMED: coefficients in the face eigenbasis of
+ *     Sec. 4.2, ut-hat = (S^T M (x) S^T M) ut per face, where the operator is
+ *     K-hat = (S^T (x) S^T) K (S (x) S) of Alg. (hdg_op_3d_transformed).      */
+typedef enum { HDG_BASIS_NODAL = 0, HDG_BASIS_TRANSFORMED = 1 } hdg_basis;
+
+typedef struct {
+  int ne[3];               /* elements per direction, each >= 1                */
+  const double* h_grid[3]; /* host; ne[d] + 1 strictly increasing coordinates  */
+  int bc[6];               /* per side x1-,x1+,x2-,x2+,x3-,x3+: 0 Dirichlet, 1 Neumann */
+} hdg_mesh;
+
+typedef struct {
+  double tau_hat;          /* penalty on the standard element, > 0 (Sec. 3.2) */
+  int mass_lumped;         /* 0: exact mass matrix (default); 1: GLL-lumped     */
+} hdg_options;
+
+typedef struct {
+  double tol;              /* stop at ||F - K ut||_2 <= tol ||F||_2 (nodal basis) */
+  int max_iter;            /* total inner CG iterations allowed per right-hand side */
+  int max_outer;           /* iterative-refinement steps allowed (>= 1)           */
+  hdg_precision inner;     /* precision of the inner CG (FP64, FP32 or BF16)      */
+  double inner_tol;        /* relative residual reduction per inner solve;
+                              <= 0 picks 1e-5 for FP32/BF16 and tol for FP64      */
+} hdg_solve_opts;
+
+typedef struct {
+  int iterations;          /* inner CG iterations                                 */
+  int outer;               /* refinement steps taken                              */
+  int applies;             /* condensed-operator applications (all precisions)    */
+  double rel_residual;     /* final FP64 ||F - K ut||_2 / ||F||_2 in the nodal basis */
+  int status;              /* hdg_status of this right-hand side                  */
+} hdg_solve_info;
+
+/* Build a context: 1D tables (GLL nodes, mass and stiffness matrices, the
+ * generalised eigen-decomposition S^T M S = I, S^T L S = Lambda of
+ * Eq. (generalized_eigenvalue_decomposition), the row matrix
+ * B_S = S^T B - S^T D M^-1 C of Eq. (hdg_bs) and the 2x2 face matrix
+ * G + C^T M^-1 C), computed on the host in FP64 and uploaded to the current
+ * device.  p in 1..16.  Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM.
+ * On success *out owns device memory until hdg_destroy.                  */
+hdg_status hdg_setup(const hdg_mesh* mesh, int p, const hdg_options* opts, hdg_ctx** out);
+
+/* Free every resource of ctx (NULL is a no-op).  Synchronises the device. */
+void hdg_destroy(hdg_ctx* ctx);
+
+size_t hdg_trace_size(const hdg_ctx* ctx);     /* unknown trace values per rhs */
+size_t hdg_volume_size(const hdg_ctx* ctx);    /* n_e n^3                      */
+size_t hdg_boundary_size(const hdg_ctx* ctx);  /* boundary data values         */
+
+/* Copy the n GLL points of the standard element [-1, 1] to h_nodes[n].   */
+hdg_status hdg_get_nodes(const hdg_ctx* ctx, double* h_nodes);
+
+/* y = K x for nrhs trace vectors with homogeneous Dirichlet data
+ * (Eq. (hdg_system); Alg. (hdg_op_3d) for HDG_BASIS_NODAL,
+ * Alg. (hdg_op_3d_transformed) for HDG_BASIS_TRANSFORMED), lambda_r =
+ * h_lambda[r] >= 0.  d_x, d_y: device, nrhs * hdg_trace_size() values of
+ * type double (FP64), float (FP32) or bfloat16 (BF16, transformed basis
+ * only); they must not overlap.  Both traces sides of a shared face are
+ * summed in a fixed order, so results are bitwise reproducible.
+ * Errors: INVALID_ARG (NULL pointer, nrhs < 1, lambda < 0, BF16 in the
+ * nodal basis), SINGULAR is not reported here, CUDA.                       */
+hdg_status hdg_apply(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_precision prec,
+                     hdg_basis basis, const void* d_x, void* d_y, void* stream);
+
+/* Solve K ut = F (Alg. (hdg_cg) with the transformed CG of
+ * Alg. (hdg_transformed_cg)) for nrhs right-hand sides, in FP64 or with an
+ * FP32/BF16 inner CG inside FP64 iterative refinement.
+ *   d_f      device, nrhs * hdg_volume_size(): nodal values of f.
+ *   d_bdry   device, nrhs * hdg_boundary_size() boundary data, or NULL (zero).
+ *   d_x0     device, nrhs * hdg_trace_size() initial traces, or NULL (zero).
+ *   d_trace  device, nrhs * hdg_trace_size(): the solution ut (nodal basis).
+ *   d_u      device, nrhs * hdg_volume_size(): recovered u, or NULL.
+ *   h_info   host array of nrhs, filled on return (the call synchronises).
+ * Returns the worst per-rhs status: SINGULAR (lambda = 0 without a
+ * Dirichlet side), NOT_CONVERGED, BREAKDOWN, INVALID_ARG, CUDA, OOM.       */
+hdg_status hdg_solve(hdg_ctx* ctx, int nrhs, const double* h_lambda, const double* d_f,
+                     const double* d_bdry, const double* d_x0, double* d_trace, double* d_u,
+                     const hdg_solve_opts* opts, hdg_solve_info* h_info, void* stream);
+
+/* Adjoint of a solve with homogeneous boundary data.  Given the forward
+ * solution d_u and the gradient d_grad_u = dL/du of a loss L(u) (both
+ * nrhs * hdg_volume_size()), solve the adjoint system -- the element system
+ * of Eq. (ldg_element_operator_threed) is symmetric, so this is the same
+ * condensed solve with volume load dL/du -- and return
+ *   d_grad_f[r]      = M_e z_{u,e}                   (dL/df, volume layout)
+ *   d_grad_lambda[r] = - sum_e z_{u,e}^T M_e u_e     (dL/dlambda, device)
+ * where z_u is the adjoint volume solution.  Errors as hdg_solve.          */
+hdg_status hdg_solve_adjoint(hdg_ctx* ctx, int nrhs, const double* h_lambda, const double* d_u,
+                             const double* d_grad_u, double* d_grad_f, double* d_grad_lambda,
+                             const hdg_solve_opts* opts, hdg_solve_info* h_info, void* stream);
+
+/* Measurement support (not part of the method).  Kernel classes:
+ *   0 condensed operator, FP32 arithmetic   1 condensed operator, FP64
+ *   2 face transforms                       3 volume transforms
+ *   4 right-hand side / recovery operator   5 CG vector and reduction kernels
+ * hdg_profile(ctx, 1) resets the counters and starts recording a CUDA event
+ * pair around every launch of classes 0-5 on the launching stream;
+ * hdg_profile(ctx, 0) stops recording.  hdg_profile_read synchronises the
+ * device and returns, for one class, the summed launch durations (ms) and
+ * the number of launches recorded; class -1 returns the number of kernel
+ * launches of all classes since the last hdg_profile(ctx, 1) (counted
+ * whether or not recording is on; time is then 0).                         */
+hdg_status hdg_profile(hdg_ctx* ctx, int enable);
+hdg_status hdg_profile_read(hdg_ctx* ctx, int kernel_class, double* total_ms, long long* launches);
+
+/* Message of the last failed call on this host thread ("" if none).      */
+const char* hdg_last_error(void);
+const char* hdg_status_string(hdg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDG_GB300_H */

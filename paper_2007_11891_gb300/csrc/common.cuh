@@ -1,0 +1,65 @@
+// Shared device-side definitions of the condensed HDG library (sm_103a).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hdg {
+
+constexpr int kMaxNDev = 17;
+
+// Cartesian mesh in the library's face-wise layout (see include/hdg.h).
+struct MeshDev {
+  int ne[3];          // elements per direction
+  int lo[3], hi[3];   // unknown planes per direction (hi < lo: none)
+  long long blk[3];   // first face id of each direction block
+  long long side[6];  // first face id of each boundary side (boundary buffer)
+  long long nfaces;   // unknown faces
+  long long nbfaces;  // boundary faces
+  int uniform;        // all elements have the same widths
+};
+
+// 1D tables of one degree in the transformed basis (Alg. hdg_op_3d_transformed):
+// c[m] = B_S[m][0] (B_S[m][1] = sigma_m c[m], sigma = +1 for m < n_even),
+// lam[m] = Lambda_m, and H = [[h0, h1], [h1, h0]] = G + C^T M^-1 C.
+template <typename T>
+struct Tables {
+  T c[kMaxNDev];
+  T h0, h1;
+};
+
+// n x n matrix passed by value (row-major).
+template <typename T>
+struct Mat1D {
+  T a[kMaxNDev * kMaxNDev];
+};
+
+// ---- storage conversions --------------------------------------------------
+template <typename ST, typename T>
+__device__ __forceinline__ T load_as(const ST* p) { return static_cast<T>(*p); }
+template <>
+__device__ __forceinline__ float load_as<__nv_bfloat16, float>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+template <typename ST, typename T>
+__device__ __forceinline__ void store_from(ST* p, T v) { *p = static_cast<ST>(v); }
+template <>
+__device__ __forceinline__ void store_from<__nv_bfloat16, float>(__nv_bfloat16* p, float v) {
+  *p = __float2bfloat16_rn(v);
+}
+
+// y += v with a single global reduction (L2 atomic).  Exactly two adds reach
+// an interior face value that starts at zero: 0 + a + b == 0 + b + a in IEEE
+// arithmetic, so the result does not depend on their order.
+__device__ __forceinline__ void red_add(double* p, double v) {
+  asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add(__nv_bfloat16* p, float v) {
+  atomicAdd(p, __float2bfloat16_rn(v));
+}
+
+}  // namespace hdg

@@ -1,0 +1,732 @@
+// C ABI of the condensed HDG library: context set-up, operator application,
+// solve (transformed CG inside FP64 iterative refinement), recovery, adjoint.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hdg.h"
+#include "internal.h"
+#include "setup1d.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hdg_status fail(hdg_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+#define HDG_CUDA(...)                                                                   \
+  do {                                                                                  \
+    cudaError_t e_ = (__VA_ARGS__);                                                     \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(e_ == cudaErrorMemoryAllocation ? HDG_ERR_OOM : HDG_ERR_CUDA,         \
+                  std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));           \
+  } while (0)
+
+#define HDG_TRY(...)                \
+  do {                              \
+    hdg_status s_ = (__VA_ARGS__);  \
+    if (s_ != HDG_OK) return s_;    \
+  } while (0)
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct hdg_ctx {
+  int device = 0;
+  int p = 0, n = 0;
+  hdg::Setup1D s1;
+  hdg::MeshDev mesh{};
+  std::vector<double> widths[3];
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  long long nelem = 0, ntrace = 0, nvol = 0, nbdry = 0;
+  int uniform = 1;
+  int has_dirichlet = 0, has_neumann = 0;
+  double* d_metric64 = nullptr;
+  float* d_metric32 = nullptr;
+  double* d_Lambda = nullptr;
+  double* d_widths = nullptr;
+  int wstride = 0;
+  hdg::Tables<double> tab64;
+  hdg::Tables<float> tab32;
+  hdg::Mat1D<double> StM, MS, S, St, M;
+  // D_Z^-1 tables for the lambdas of the last call, per precision
+  std::vector<double> lam64, lam32;
+  DevBuf dinv64, dinv32, lam_dev;
+  // workspaces
+  DevBuf ws[24];
+  DevBuf partials, counters, cgs, flags, scal;
+  int red_blocks = 0;
+  // measurement: launch count and optional event pairs per kernel class
+  bool prof_on = false;
+  long long launches = 0;
+  std::vector<cudaEvent_t> ev[6];
+  size_t ev_used[6] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+enum Ws {
+  W_XHAT = 0, W_YHAT, W_FHAT_T, W_RHAT, W_TMP, W_FVOL, W_GHAT, W_WVOL,
+  W_R, W_D, W_P, W_Q, W_DOT, W_DOT2
+};
+
+hdg_status ensure(DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return HDG_OK;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return fail(HDG_ERR_OOM, std::string("cudaMalloc workspace: ") + cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  return HDG_OK;
+}
+
+template <typename T>
+T* wsp(hdg_ctx* c, int i) { return static_cast<T*>(c->ws[i].p); }
+
+enum KernelClass { K_OP32 = 0, K_OP64 = 1, K_FACE = 2, K_VOL = 3, K_RHS = 4, K_VEC = 5 };
+
+// Counts a launch and, while profiling, brackets it with an event pair.
+struct Timed {
+  hdg_ctx* c;
+  int cls;
+  cudaStream_t s;
+  long long idx = -1;
+  Timed(hdg_ctx* c_, int cls_, cudaStream_t s_) : c(c_), cls(cls_), s(s_) {
+    c->launches += 1;
+    if (!c->prof_on) return;
+    std::vector<cudaEvent_t>& v = c->ev[cls];
+    if (2 * c->ev_used[cls] + 2 > v.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+      v.push_back(a);
+      v.push_back(b);
+    }
+    idx = (long long)c->ev_used[cls]++;
+    cudaEventRecord(v[2 * idx], s);
+  }
+  ~Timed() {
+    if (idx >= 0) cudaEventRecord(c->ev[cls][2 * idx + 1], s);
+  }
+};
+
+template <typename T>
+const T* metric_ptr(const hdg_ctx* c);
+template <>
+const double* metric_ptr<double>(const hdg_ctx* c) { return c->d_metric64; }
+template <>
+const float* metric_ptr<float>(const hdg_ctx* c) { return c->d_metric32; }
+
+template <typename T>
+const hdg::Tables<T>& tables(const hdg_ctx* c);
+template <>
+const hdg::Tables<double>& tables<double>(const hdg_ctx* c) { return c->tab64; }
+template <>
+const hdg::Tables<float>& tables<float>(const hdg_ctx* c) { return c->tab32; }
+
+long long nclass(const hdg_ctx* c) { return c->uniform ? 1 : c->nelem; }
+long long n3(const hdg_ctx* c) { return (long long)c->n * c->n * c->n; }
+
+// D_Z^-1 tables for the given lambdas (rebuilt when they change)
+template <typename T>
+hdg_status ensure_dinv(hdg_ctx* c, int nrhs, const double* lam, cudaStream_t s, const T** out) {
+  std::vector<double>& cur = sizeof(T) == 8 ? c->lam64 : c->lam32;
+  DevBuf& buf = sizeof(T) == 8 ? c->dinv64 : c->dinv32;
+  std::vector<double> want(lam, lam + nrhs);
+  if (cur != want) {
+    HDG_TRY(ensure(buf, sizeof(T) * (size_t)nrhs * nclass(c) * n3(c)));
+    HDG_TRY(ensure(c->lam_dev, sizeof(double) * nrhs));
+    HDG_CUDA(cudaMemcpyAsync(c->lam_dev.p, lam, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    HDG_CUDA(hdg::launch_dinv<T>(c->n, static_cast<double*>(c->lam_dev.p), nrhs, c->d_metric64, nclass(c),
+                                 c->d_Lambda, static_cast<T*>(buf.p), s));
+    // the lambda buffer is reused by later calls: finish the table first
+    HDG_CUDA(cudaStreamSynchronize(s));
+    cur = want;
+  }
+  *out = static_cast<const T*>(buf.p);
+  return HDG_OK;
+}
+
+template <typename T, typename ST>
+hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv) {
+  hdg::TptArgs<T, ST> a{};
+  a.mesh = c->mesh;
+  a.tab = tables<T>(c);
+  a.metric = metric_ptr<T>(c);
+  a.dinv = dinv;
+  a.dinv_rhs_stride = nclass(c) * n3(c);
+  a.trace_stride = c->ntrace;
+  a.bdry_stride = c->nbdry;
+  a.vol_stride = c->nvol;
+  a.ppb = hdg::tpt_ppb(c->n);
+  a.npencils = (long long)c->mesh.ne[1] * c->mesh.ne[2];
+  return a;
+}
+
+// zero the x2/x3 blocks of nrhs trace vectors (x1 faces are stored, not added)
+template <typename ST>
+hdg_status zero_x23(const hdg_ctx* c, ST* y, int nrhs, cudaStream_t s) {
+  const long long off = c->mesh.blk[1] * (long long)c->n * c->n;
+  const long long cnt = c->ntrace - off;
+  if (cnt <= 0) return HDG_OK;
+  HDG_CUDA(cudaMemset2DAsync(y + off, sizeof(ST) * c->ntrace, 0, sizeof(ST) * cnt, nrhs, s));
+  return HDG_OK;
+}
+
+template <typename T, typename ST>
+hdg_status tpt_apply(hdg_ctx* c, int nrhs, const T* dinv, const ST* x, ST* y, cudaStream_t s,
+                     const int* skip = nullptr, hdg::CgHook hook = hdg::CgHook{}) {
+  HDG_TRY(zero_x23<ST>(c, y, nrhs, s));
+  hdg::TptArgs<T, ST> a = base_args<T, ST>(c, dinv);
+  a.x = x;
+  a.y = y;
+  a.skip = skip;
+  a.hook = hook;
+  Timed t(c, sizeof(T) == 8 ? K_OP64 : K_OP32, s);
+  HDG_CUDA(hdg::launch_tpt<T, ST>(hdg::TPT_APPLY, c->n, a, nrhs, s));
+  return HDG_OK;
+}
+
+hdg_status check_lambda(const hdg_ctx* c, int nrhs, const double* lam) {
+  if (!lam) return fail(HDG_ERR_INVALID_ARG, "lambda pointer is NULL");
+  for (int r = 0; r < nrhs; ++r)
+    if (!(lam[r] >= 0.0) || !std::isfinite(lam[r])) return fail(HDG_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  (void)c;
+  return HDG_OK;
+}
+
+int reduction_blocks(long long len) {
+  long long b = (len + 255) / 256;
+  return (int)std::max(1LL, std::min(b, 152LL * 4));
+}
+
+hdg_status ensure_reductions(hdg_ctx* c, int nrhs) {
+  c->red_blocks = 152 * 8;   // upper bound on blocks of any reducing launch
+  const long long tpt_b = hdg::tpt_blocks((long long)c->mesh.ne[1] * c->mesh.ne[2], hdg::tpt_ppb(c->n));
+  const long long pb = std::max<long long>(c->red_blocks, tpt_b);
+  HDG_TRY(ensure(c->partials, sizeof(double) * (size_t)nrhs * pb));
+  const bool fresh = c->counters.bytes < sizeof(unsigned int) * (size_t)nrhs;
+  HDG_TRY(ensure(c->counters, sizeof(unsigned int) * (size_t)nrhs));
+  if (fresh) HDG_CUDA(cudaMemset(c->counters.p, 0, c->counters.bytes));
+  HDG_TRY(ensure(c->cgs, sizeof(hdg::CgScalars) * (size_t)nrhs));
+  HDG_TRY(ensure(c->flags, sizeof(int) * (size_t)nrhs));
+  HDG_TRY(ensure(c->scal, sizeof(double) * (size_t)nrhs * 4));
+  return HDG_OK;
+}
+
+template <typename T>
+hdg_status dot(hdg_ctx* c, const T* a, const T* b, long long len, int nrhs, double* out, cudaStream_t s) {
+  Timed t(c, K_VEC, s);
+  HDG_CUDA(hdg::launch_dot<T>(a, b, len, nrhs, static_cast<double*>(c->partials.p),
+                              static_cast<unsigned int*>(c->counters.p), out, reduction_blocks(len), s));
+  return HDG_OK;
+}
+
+// Inner CG on K-hat d = rhat in precision T for the right-hand sides with
+// active[r] != 0; returns per-rhs iterations and status.
+template <typename T>
+hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat, double tol_inner,
+                    const std::vector<int>& active, const std::vector<int>& max_it,
+                    std::vector<int>& iters, std::vector<int>& status, cudaStream_t s) {
+  const long long T_ = c->ntrace;
+  const long long tot = T_ * nrhs;
+  for (int i : {W_R, W_D, W_P, W_Q}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
+  T* r = wsp<T>(c, W_R);
+  T* d = wsp<T>(c, W_D);
+  T* p = wsp<T>(c, W_P);
+  T* q = wsp<T>(c, W_Q);
+  const T* dinv = nullptr;
+  HDG_TRY(ensure_dinv<T>(c, nrhs, lam, s, &dinv));
+  double* rr0 = static_cast<double*>(c->scal.p);
+  double* pq = rr0 + nrhs;
+  int* flags = static_cast<int*>(c->flags.p);
+  hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
+
+  if (sizeof(T) == 8) HDG_CUDA(cudaMemcpyAsync(r, rhat, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+  else { Timed t_(c, K_VEC, s); HDG_CUDA((hdg::launch_convert<double, float>(rhat, reinterpret_cast<float*>(r), tot, s))); }
+  HDG_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * tot, s));
+  HDG_CUDA(cudaMemcpyAsync(p, r, sizeof(T) * tot, cudaMemcpyDeviceToDevice, s));
+  HDG_TRY(dot<T>(c, r, r, T_, nrhs, rr0, s));
+  std::vector<int> hflags(nrhs);
+  int maxit = 0;
+  for (int i = 0; i < nrhs; ++i) {
+    hflags[i] = active[i] ? 0 : 1;
+    maxit = std::max(maxit, max_it[i]);
+  }
+  HDG_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+  // the per-rhs cap is the largest; per-rhs caps below it are enforced on the host afterwards
+  { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_init(cg, flags, rr0, tol_inner, maxit, nrhs, s)); }
+  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), pq};
+  const int vb = reduction_blocks(T_);
+  const int chunk = 16;
+  std::vector<hdg::CgScalars> hcg(nrhs);
+  for (int done_it = 0; done_it < maxit; done_it += chunk) {
+    for (int k = 0; k < chunk; ++k) {
+      HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, p, q, s, flags, hook)));
+      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_update<T>(cg, flags, pq, d, r, p, q, T_, nrhs, static_cast<double*>(c->partials.p),
+                                        static_cast<unsigned int*>(c->counters.p), vb, s)); }
+      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, T_, nrhs, s)); }
+    }
+    HDG_CUDA(cudaMemcpyAsync(hflags.data(), flags, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
+    HDG_CUDA(cudaStreamSynchronize(s));
+    bool all = true;
+    for (int i = 0; i < nrhs; ++i) all = all && hflags[i];
+    if (all) break;
+  }
+  HDG_CUDA(cudaMemcpyAsync(hcg.data(), cg, sizeof(hdg::CgScalars) * nrhs, cudaMemcpyDeviceToHost, s));
+  HDG_CUDA(cudaStreamSynchronize(s));
+  iters.assign(nrhs, 0);
+  status.assign(nrhs, HDG_OK);
+  for (int i = 0; i < nrhs; ++i) {
+    if (!active[i]) continue;
+    iters[i] = hcg[i].it;
+    status[i] = hcg[i].status == 6 ? HDG_ERR_BREAKDOWN : (hcg[i].done ? HDG_OK : HDG_ERR_NOT_CONVERGED);
+    if (hcg[i].status == 5) status[i] = HDG_ERR_NOT_CONVERGED;
+  }
+  return HDG_OK;
+}
+
+// Full solve; `adjoint_load` selects f-hat = (S^T)^(x3) b instead of d0 (S^T M)^(x3) f.
+hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol_in, bool adjoint_load,
+                      const double* bdry, const double* x0, double* trace_out, double* u_out,
+                      const hdg_solve_opts* opts, hdg_solve_info* info, cudaStream_t s) {
+  const long long T_ = c->ntrace, V = c->nvol, B = c->nbdry;
+  const int n = c->n;
+  hdg_solve_opts o;
+  if (opts) o = *opts;
+  else { o.tol = 1e-10; o.max_iter = 10000; o.max_outer = 20; o.inner = HDG_FP64; o.inner_tol = 0.0; }
+  if (!(o.tol > 0.0) || o.max_iter < 1 || o.max_outer < 1) return fail(HDG_ERR_INVALID_ARG, "bad solve options");
+  if (o.inner == HDG_BF16) return fail(HDG_ERR_UNSUPPORTED, "BF16 inner solve is not available");
+  double tol_inner = o.inner_tol > 0.0 ? o.inner_tol : (o.inner == HDG_FP64 ? 0.1 * o.tol : 1e-5);
+  for (int r = 0; r < nrhs; ++r)
+    if (lam[r] == 0.0 && !c->has_dirichlet)
+      return fail(HDG_ERR_SINGULAR, "lambda = 0 without a Dirichlet side: the condensed operator is singular");
+  const long long tot = T_ * nrhs;
+  for (int i : {W_XHAT, W_YHAT, W_FHAT_T, W_RHAT, W_TMP}) HDG_TRY(ensure(c->ws[i], sizeof(double) * (size_t)tot));
+  HDG_TRY(ensure(c->ws[W_FVOL], sizeof(double) * (size_t)V * nrhs));
+  HDG_TRY(ensure(c->ws[W_GHAT], sizeof(double) * (size_t)std::max<long long>(B, 1) * nrhs));
+  HDG_TRY(ensure(c->ws[W_DOT], sizeof(double) * nrhs * 2));
+  HDG_TRY(ensure_reductions(c, nrhs));
+  double* xhat = wsp<double>(c, W_XHAT);
+  double* yhat = wsp<double>(c, W_YHAT);
+  double* Fhat = wsp<double>(c, W_FHAT_T);
+  double* rhat = wsp<double>(c, W_RHAT);
+  double* tmp = wsp<double>(c, W_TMP);
+  double* fhat = wsp<double>(c, W_FVOL);
+  double* ghat = bdry ? wsp<double>(c, W_GHAT) : nullptr;
+  double* dots = wsp<double>(c, W_DOT);
+  const double* dinv = nullptr;
+  HDG_TRY(ensure_dinv<double>(c, nrhs, lam, s, &dinv));
+
+  // 1. f-hat in the element eigenspace
+  if (adjoint_load)
+    { Timed t_(c, K_VOL, s); HDG_CUDA(hdg::launch_volume_transform(n, vol_in, fhat, c->nelem, nrhs, V, c->St, c->d_metric64, c->uniform, 0, s)); }
+  else
+    { Timed t_(c, K_VOL, s); HDG_CUDA(hdg::launch_volume_transform(n, vol_in, fhat, c->nelem, nrhs, V, c->StM, c->d_metric64, c->uniform, 1, s)); }
+  // 2. boundary data in the face eigenbasis
+  if (bdry)
+    { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<double, double>(n, bdry, ghat, c->mesh.nbfaces, nrhs, B, B, c->StM, 1.0, 0, s))); }
+  // 3. transformed right-hand side with Dirichlet lift and Neumann load
+  {
+    HDG_TRY(zero_x23<double>(c, Fhat, nrhs, s));
+    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv);
+    a.y = Fhat;
+    a.gbd = ghat;
+    a.src = fhat;
+    { Timed t_(c, K_RHS, s); HDG_CUDA((hdg::launch_tpt<double, double>(hdg::TPT_RHS, n, a, nrhs, s))); }
+    if (bdry && c->has_neumann)
+      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_neumann_add(c->mesh, n, c->d_widths, c->wstride, ghat, Fhat, nrhs, B, T_, s)); }
+  }
+  // 4. ||F|| in the nodal basis: F = (M S (x) M S) F-hat
+  { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<double, double>(n, Fhat, tmp, c->mesh.nfaces, nrhs, T_, T_, c->MS, 1.0, 0, s))); }
+  HDG_TRY(dot<double>(c, tmp, tmp, T_, nrhs, dots, s));
+  std::vector<double> normF2(nrhs), normR2(nrhs);
+  HDG_CUDA(cudaMemcpyAsync(normF2.data(), dots, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+  HDG_CUDA(cudaStreamSynchronize(s));
+  // 5. initial guess
+  if (x0)
+    { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<double, double>(n, x0, xhat, c->mesh.nfaces, nrhs, T_, T_, c->StM, 1.0, 0, s))); }
+  else
+    HDG_CUDA(cudaMemsetAsync(xhat, 0, sizeof(double) * tot, s));
+
+  std::vector<int> active(nrhs, 1), total_it(nrhs, 0), outer(nrhs, 0), applies(nrhs, 1), status(nrhs, HDG_OK);
+  std::vector<double> relres(nrhs, 0.0);
+  bool zero_x = (x0 == nullptr);
+  for (int step = 0; step <= o.max_outer; ++step) {
+    // residual r-hat = F-hat - K-hat x-hat (FP64)
+    if (zero_x) {
+      HDG_CUDA(cudaMemcpyAsync(rhat, Fhat, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+    } else {
+      HDG_TRY((tpt_apply<double, double>(c, nrhs, dinv, xhat, yhat, s)));
+      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_sub(Fhat, yhat, rhat, tot, s)); }
+      for (int r = 0; r < nrhs; ++r) applies[r] += active[r];
+    }
+    { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<double, double>(n, rhat, tmp, c->mesh.nfaces, nrhs, T_, T_, c->MS, 1.0, 0, s))); }
+    HDG_TRY(dot<double>(c, tmp, tmp, T_, nrhs, dots, s));
+    HDG_CUDA(cudaMemcpyAsync(normR2.data(), dots, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, s));
+    HDG_CUDA(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!active[r]) continue;
+      relres[r] = normF2[r] > 0.0 ? std::sqrt(normR2[r] / normF2[r]) : std::sqrt(normR2[r]);
+      const bool ok = normF2[r] > 0.0 ? normR2[r] <= o.tol * o.tol * normF2[r] : normR2[r] == 0.0;
+      if (ok || !std::isfinite(relres[r])) {
+        active[r] = 0;
+        if (!std::isfinite(relres[r])) status[r] = HDG_ERR_BREAKDOWN;
+      } else if (step == o.max_outer || total_it[r] >= o.max_iter) {
+        active[r] = 0;
+        status[r] = HDG_ERR_NOT_CONVERGED;
+      }
+      any = any || active[r];
+    }
+    if (!any) break;
+    std::vector<int> caps(nrhs), it, st;
+    for (int r = 0; r < nrhs; ++r) caps[r] = std::max(0, o.max_iter - total_it[r]);
+    // inner solve K-hat d = r-hat; d is left in W_D
+    if (o.inner == HDG_FP64) {
+      HDG_TRY(inner_cg<double>(c, nrhs, lam, rhat, tol_inner, active, caps, it, st, s));
+      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_to<double>(xhat, wsp<double>(c, W_D), tot, s)); }
+    } else {
+      HDG_TRY(inner_cg<float>(c, nrhs, lam, rhat, tol_inner, active, caps, it, st, s));
+      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_to<float>(xhat, wsp<float>(c, W_D), tot, s)); }
+    }
+    zero_x = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!active[r]) continue;
+      total_it[r] += it[r];
+      applies[r] += it[r];
+      outer[r] += 1;
+      if (st[r] == HDG_ERR_BREAKDOWN) { status[r] = HDG_ERR_BREAKDOWN; active[r] = 0; }
+    }
+  }
+  // 6. traces in the nodal basis, u by recovery
+  { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<double, double>(n, xhat, trace_out, c->mesh.nfaces, nrhs, T_, T_, c->S, 1.0, 0, s))); }
+  if (u_out) {
+    HDG_TRY(ensure(c->ws[W_WVOL], sizeof(double) * (size_t)V * nrhs));
+    double* w = wsp<double>(c, W_WVOL);
+    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv);
+    a.x = xhat;
+    a.gbd = ghat;
+    a.src = fhat;
+    a.vout = w;
+    { Timed t_(c, K_RHS, s); HDG_CUDA((hdg::launch_tpt<double, double>(hdg::TPT_RECOVER, n, a, nrhs, s))); }
+    { Timed t_(c, K_VOL, s); HDG_CUDA(hdg::launch_volume_transform(n, w, u_out, c->nelem, nrhs, V, c->S, c->d_metric64, c->uniform, 0, s)); }
+  }
+  HDG_CUDA(cudaStreamSynchronize(s));
+  hdg_status worst = HDG_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    if (info) {
+      info[r].iterations = total_it[r];
+      info[r].outer = outer[r];
+      info[r].applies = applies[r];
+      info[r].rel_residual = relres[r];
+      info[r].status = status[r];
+    }
+    if (status[r] != HDG_OK && worst == HDG_OK) worst = (hdg_status)status[r];
+  }
+  if (worst != HDG_OK) return fail(worst, "solve did not reach the tolerance for every right-hand side");
+  return HDG_OK;
+}
+
+__global__ void negate_kernel(double* x, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = -x[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* hdg_last_error(void) { return g_last_error.c_str(); }
+
+hdg_status hdg_profile(hdg_ctx* c, int enable) {
+  if (!c) return fail(HDG_ERR_INVALID_ARG, "NULL context");
+  if (enable) {
+    c->launches = 0;
+    for (int k = 0; k < 6; ++k) c->ev_used[k] = 0;
+  }
+  c->prof_on = enable != 0;
+  return HDG_OK;
+}
+
+hdg_status hdg_profile_read(hdg_ctx* c, int cls, double* total_ms, long long* launches) {
+  if (!c || !total_ms || !launches || cls < -1 || cls > 5) return fail(HDG_ERR_INVALID_ARG, "bad profile query");
+  HDG_CUDA(cudaDeviceSynchronize());
+  if (cls == -1) {
+    *total_ms = 0.0;
+    *launches = c->launches;
+    return HDG_OK;
+  }
+  double tot = 0.0;
+  for (size_t i = 0; i < c->ev_used[cls]; ++i) {
+    float ms = 0.f;
+    HDG_CUDA(cudaEventElapsedTime(&ms, c->ev[cls][2 * i], c->ev[cls][2 * i + 1]));
+    tot += ms;
+  }
+  *total_ms = tot;
+  *launches = (long long)c->ev_used[cls];
+  return HDG_OK;
+}
+
+const char* hdg_status_string(hdg_status s) {
+  switch (s) {
+    case HDG_OK: return "ok";
+    case HDG_ERR_INVALID_ARG: return "invalid argument";
+    case HDG_ERR_SINGULAR: return "singular operator (lambda = 0 without Dirichlet data)";
+    case HDG_ERR_CUDA: return "CUDA error";
+    case HDG_ERR_OOM: return "out of device memory";
+    case HDG_ERR_NOT_CONVERGED: return "not converged";
+    case HDG_ERR_BREAKDOWN: return "CG breakdown";
+    case HDG_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+hdg_status hdg_setup(const hdg_mesh* mesh, int p, const hdg_options* opts, hdg_ctx** out) {
+  g_last_error.clear();
+  if (!mesh || !out) return fail(HDG_ERR_INVALID_ARG, "mesh and out must not be NULL");
+  *out = nullptr;
+  if (p < 1 || p > 16) return fail(HDG_ERR_UNSUPPORTED, "degree p must be in 1..16");
+  const double tau_hat = opts ? opts->tau_hat : 25.0;
+  const int lumped = opts ? opts->mass_lumped : 0;
+  for (int d = 0; d < 3; ++d) {
+    if (mesh->ne[d] < 1 || !mesh->h_grid[d]) return fail(HDG_ERR_INVALID_ARG, "each direction needs >= 1 element and a grid");
+    for (int i = 0; i < mesh->ne[d]; ++i)
+      if (!(mesh->h_grid[d][i + 1] > mesh->h_grid[d][i])) return fail(HDG_ERR_INVALID_ARG, "grid lines must increase");
+  }
+  for (int sd = 0; sd < 6; ++sd)
+    if (mesh->bc[sd] != 0 && mesh->bc[sd] != 1) return fail(HDG_ERR_INVALID_ARG, "bc must be 0 (Dirichlet) or 1 (Neumann)");
+  int dev = 0;
+  HDG_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  HDG_CUDA(cudaGetDeviceProperties(&prop, dev));
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(HDG_ERR_UNSUPPORTED, "this library is built for sm_103 (GB300) only");
+
+  hdg_ctx* c = new hdg_ctx();
+  c->device = dev;
+  c->p = p;
+  c->n = p + 1;
+  const char* msg = "";
+  if (hdg::build_setup1d(p, tau_hat, lumped, &c->s1, &msg) != 0) {
+    delete c;
+    return fail(HDG_ERR_INVALID_ARG, std::string("1D set-up: ") + msg);
+  }
+  const int n = c->n;
+  hdg::MeshDev& m = c->mesh;
+  long long off = 0;
+  for (int d = 0; d < 3; ++d) {
+    m.ne[d] = mesh->ne[d];
+    c->widths[d].resize(mesh->ne[d]);
+    for (int i = 0; i < mesh->ne[d]; ++i) c->widths[d][i] = mesh->h_grid[d][i + 1] - mesh->h_grid[d][i];
+  }
+  for (int sd = 0; sd < 6; ++sd) {
+    c->bc[sd] = mesh->bc[sd];
+    if (mesh->bc[sd] == 0) c->has_dirichlet = 1;
+    else c->has_neumann = 1;
+  }
+  for (int d = 0; d < 3; ++d) {
+    const int a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
+    m.lo[d] = c->bc[2 * d] == 1 ? 0 : 1;
+    m.hi[d] = c->bc[2 * d + 1] == 1 ? m.ne[d] : m.ne[d] - 1;
+    m.blk[d] = off;
+    const long long np = std::max(0, m.hi[d] - m.lo[d] + 1);
+    off += np * m.ne[a] * m.ne[b];
+  }
+  m.nfaces = off;
+  off = 0;
+  for (int sd = 0; sd < 6; ++sd) {
+    const int d = sd / 2, a = d == 0 ? 1 : 0, b = d == 2 ? 1 : 2;
+    m.side[sd] = off;
+    off += (long long)m.ne[a] * m.ne[b];
+  }
+  m.nbfaces = off;
+  c->nelem = (long long)m.ne[0] * m.ne[1] * m.ne[2];
+  c->ntrace = m.nfaces * n * n;
+  c->nvol = c->nelem * n * n * n;
+  c->nbdry = m.nbfaces * n * n;
+  // uniform: every direction has constant width (to round-off) -> one element class
+  bool uni = true;
+  for (int d = 0; d < 3; ++d)
+    for (double w : c->widths[d]) uni = uni && std::fabs(w - c->widths[d][0]) <= 1e-14 * c->widths[d][0];
+  c->uniform = uni ? 1 : 0;
+  m.uniform = c->uniform;
+  // metric factors d0..d3 of Sec. 3.2 per element (or the single class)
+  const long long ncls = uni ? 1 : c->nelem;
+  std::vector<double> met(4 * ncls);
+  std::vector<float> met32(4 * ncls);
+  for (long long e = 0; e < ncls; ++e) {
+    const int e1 = (int)(e % m.ne[0]), e2 = (int)((e / m.ne[0]) % m.ne[1]), e3 = (int)(e / ((long long)m.ne[0] * m.ne[1]));
+    const double h1 = c->widths[0][e1], h2 = c->widths[1][e2], h3 = c->widths[2][e3];
+    const double d0 = h1 * h2 * h3 / 8.0;
+    met[4 * e + 0] = d0;
+    met[4 * e + 1] = d0 * (2.0 / h1) * (2.0 / h1);
+    met[4 * e + 2] = d0 * (2.0 / h2) * (2.0 / h2);
+    met[4 * e + 3] = d0 * (2.0 / h3) * (2.0 / h3);
+    for (int k = 0; k < 4; ++k) met32[4 * e + k] = (float)met[4 * e + k];
+  }
+  c->wstride = std::max(m.ne[0], std::max(m.ne[1], m.ne[2]));
+  std::vector<double> wid(3 * c->wstride, 0.0);
+  for (int d = 0; d < 3; ++d)
+    for (int i = 0; i < m.ne[d]; ++i) wid[d * c->wstride + i] = c->widths[d][i];
+  auto up = [&](void** dst, const void* src, size_t bytes) -> hdg_status {
+    cudaError_t e = cudaMalloc(dst, bytes);
+    if (e != cudaSuccess) return fail(HDG_ERR_OOM, "cudaMalloc tables");
+    e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(HDG_ERR_CUDA, "upload tables");
+    return HDG_OK;
+  };
+  hdg_status st = HDG_OK;
+  if (st == HDG_OK) st = up((void**)&c->d_metric64, met.data(), sizeof(double) * met.size());
+  if (st == HDG_OK) st = up((void**)&c->d_metric32, met32.data(), sizeof(float) * met32.size());
+  if (st == HDG_OK) st = up((void**)&c->d_Lambda, c->s1.Lambda, sizeof(double) * n);
+  if (st == HDG_OK) st = up((void**)&c->d_widths, wid.data(), sizeof(double) * wid.size());
+  if (st != HDG_OK) {
+    hdg_destroy(c);
+    return st;
+  }
+  for (int i = 0; i < n; ++i) {
+    c->tab64.c[i] = c->s1.bs[i];
+    c->tab32.c[i] = (float)c->s1.bs[i];
+  }
+  c->tab64.h0 = c->s1.h0;
+  c->tab64.h1 = c->s1.h1;
+  c->tab32.h0 = (float)c->s1.h0;
+  c->tab32.h1 = (float)c->s1.h1;
+  for (int i = 0; i < n * n; ++i) {
+    c->StM.a[i] = c->s1.StM[i];
+    c->MS.a[i] = c->s1.MS[i];
+    c->St.a[i] = c->s1.St[i];
+    c->M.a[i] = c->s1.M[i];
+  }
+  // S as the matrix acting on a vector of mode coefficients: (S)[node][mode]
+  for (int i = 0; i < n; ++i)
+    for (int mm = 0; mm < n; ++mm) c->S.a[i * n + mm] = c->s1.S[i * n + mm];
+  *out = c;
+  return HDG_OK;
+}
+
+void hdg_destroy(hdg_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  cudaFree(c->d_metric64);
+  cudaFree(c->d_metric32);
+  cudaFree(c->d_Lambda);
+  cudaFree(c->d_widths);
+  for (DevBuf* b : {&c->dinv64, &c->dinv32, &c->lam_dev, &c->partials, &c->counters, &c->cgs, &c->flags, &c->scal})
+    if (b->p) cudaFree(b->p);
+  for (DevBuf& b : c->ws)
+    if (b.p) cudaFree(b.p);
+  for (auto& v : c->ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+  delete c;
+}
+
+size_t hdg_trace_size(const hdg_ctx* c) { return c ? (size_t)c->ntrace : 0; }
+size_t hdg_volume_size(const hdg_ctx* c) { return c ? (size_t)c->nvol : 0; }
+size_t hdg_boundary_size(const hdg_ctx* c) { return c ? (size_t)c->nbdry : 0; }
+
+hdg_status hdg_get_nodes(const hdg_ctx* c, double* h_nodes) {
+  if (!c || !h_nodes) return fail(HDG_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(h_nodes, c->s1.nodes, sizeof(double) * c->n);
+  return HDG_OK;
+}
+
+hdg_status hdg_apply(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precision prec, hdg_basis basis,
+                     const void* d_x, void* d_y, void* stream) {
+  g_last_error.clear();
+  if (!c || !d_x || !d_y || nrhs < 1) return fail(HDG_ERR_INVALID_ARG, "NULL pointer or nrhs < 1");
+  HDG_TRY(check_lambda(c, nrhs, h_lambda));
+  if (basis != HDG_BASIS_NODAL && basis != HDG_BASIS_TRANSFORMED) return fail(HDG_ERR_INVALID_ARG, "bad basis");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long tot = c->ntrace * nrhs;
+  const int n = c->n;
+  if (prec == HDG_FP64) {
+    const double* dinv = nullptr;
+    HDG_TRY(ensure_dinv<double>(c, nrhs, h_lambda, s, &dinv));
+    if (basis == HDG_BASIS_TRANSFORMED)
+      return tpt_apply<double, double>(c, nrhs, dinv, static_cast<const double*>(d_x), static_cast<double*>(d_y), s);
+    HDG_TRY(ensure(c->ws[W_XHAT], sizeof(double) * tot));
+    HDG_TRY(ensure(c->ws[W_YHAT], sizeof(double) * tot));
+    double* xh = wsp<double>(c, W_XHAT);
+    double* yh = wsp<double>(c, W_YHAT);
+    { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<double, double>(n, static_cast<const double*>(d_x), xh, c->mesh.nfaces,
+                                                          nrhs, c->ntrace, c->ntrace, c->StM, 1.0, 0, s))); }
+    HDG_TRY((tpt_apply<double, double>(c, nrhs, dinv, xh, yh, s)));
+    { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<double, double>(n, yh, static_cast<double*>(d_y), c->mesh.nfaces, nrhs,
+                                                          c->ntrace, c->ntrace, c->MS, 1.0, 0, s))); }
+    return HDG_OK;
+  }
+  if (prec == HDG_FP32) {
+    const float* dinv = nullptr;
+    HDG_TRY(ensure_dinv<float>(c, nrhs, h_lambda, s, &dinv));
+    if (basis == HDG_BASIS_TRANSFORMED)
+      return tpt_apply<float, float>(c, nrhs, dinv, static_cast<const float*>(d_x), static_cast<float*>(d_y), s);
+    HDG_TRY(ensure(c->ws[W_XHAT], sizeof(float) * tot));
+    HDG_TRY(ensure(c->ws[W_YHAT], sizeof(float) * tot));
+    float* xh = wsp<float>(c, W_XHAT);
+    float* yh = wsp<float>(c, W_YHAT);
+    { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<float, float>(n, static_cast<const float*>(d_x), xh, c->mesh.nfaces, nrhs,
+                                                        c->ntrace, c->ntrace, c->StM, 1.0, 0, s))); }
+    HDG_TRY((tpt_apply<float, float>(c, nrhs, dinv, xh, yh, s)));
+    { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<float, float>(n, yh, static_cast<float*>(d_y), c->mesh.nfaces, nrhs,
+                                                        c->ntrace, c->ntrace, c->MS, 1.0, 0, s))); }
+    return HDG_OK;
+  }
+  return fail(HDG_ERR_UNSUPPORTED, "BF16 apply is not available");
+}
+
+hdg_status hdg_solve(hdg_ctx* c, int nrhs, const double* h_lambda, const double* d_f, const double* d_bdry,
+                     const double* d_x0, double* d_trace, double* d_u, const hdg_solve_opts* opts,
+                     hdg_solve_info* h_info, void* stream) {
+  g_last_error.clear();
+  if (!c || !d_f || !d_trace || nrhs < 1) return fail(HDG_ERR_INVALID_ARG, "NULL pointer or nrhs < 1");
+  HDG_TRY(check_lambda(c, nrhs, h_lambda));
+  return solve_impl(c, nrhs, h_lambda, d_f, false, d_bdry, d_x0, d_trace, d_u, opts, h_info,
+                    static_cast<cudaStream_t>(stream));
+}
+
+hdg_status hdg_solve_adjoint(hdg_ctx* c, int nrhs, const double* h_lambda, const double* d_u,
+                             const double* d_grad_u, double* d_grad_f, double* d_grad_lambda,
+                             const hdg_solve_opts* opts, hdg_solve_info* h_info, void* stream) {
+  g_last_error.clear();
+  if (!c || !d_u || !d_grad_u || !d_grad_f || !d_grad_lambda || nrhs < 1)
+    return fail(HDG_ERR_INVALID_ARG, "NULL pointer or nrhs < 1");
+  HDG_TRY(check_lambda(c, nrhs, h_lambda));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long V = c->nvol;
+  HDG_TRY(ensure(c->ws[W_DOT2], sizeof(double) * (size_t)V * nrhs));
+  HDG_TRY(ensure(c->ws[W_WVOL], sizeof(double) * (size_t)V * nrhs));
+  HDG_TRY(ensure(c->ws[W_TMP], sizeof(double) * (size_t)c->ntrace * nrhs));
+  // adjoint traces are not returned: solve into a scratch trace buffer
+  DevBuf tr;
+  HDG_TRY(ensure(tr, sizeof(double) * (size_t)c->ntrace * nrhs));
+  double* z = wsp<double>(c, W_DOT2);
+  hdg_status st = solve_impl(c, nrhs, h_lambda, d_grad_u, true, nullptr, nullptr, static_cast<double*>(tr.p), z,
+                             opts, h_info, s);
+  cudaFree(tr.p);
+  if (st != HDG_OK) return st;
+  // dL/df = M_e z_u = d0 (M (x) M (x) M) z_u ;  dL/dlambda = - (M_e z_u) . u
+  { Timed t_(c, K_VOL, s); HDG_CUDA(hdg::launch_volume_transform(c->n, z, d_grad_f, c->nelem, nrhs, V, c->M, c->d_metric64, c->uniform, 1, s)); }
+  HDG_TRY(ensure_reductions(c, nrhs));
+  HDG_TRY(dot<double>(c, d_grad_f, d_u, V, nrhs, d_grad_lambda, s));
+  { Timed t_(c, K_VEC, s); negate_kernel<<<(nrhs + 127) / 128, 128, 0, s>>>(d_grad_lambda, nrhs); }
+  HDG_CUDA(cudaGetLastError());
+  HDG_CUDA(cudaStreamSynchronize(s));
+  return HDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Host-side launchers shared between the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "tpt_kernel.cuh"
+
+namespace hdg {
+
+// ---- condensed operator (tpt_*.cu) -----------------------------------------
+// Launches tpt_kernel<T, ST, n, mode> over all x1-pencils for nrhs right-hand
+// sides.  The caller zeroes the x2/x3 blocks of the output first (APPLY, RHS).
+template <typename T, typename ST>
+cudaError_t launch_tpt(int mode, int n, TptArgs<T, ST> a, int nrhs, cudaStream_t s);
+
+// pencils per block and threads per block for degree n
+int tpt_ppb(int n);
+int tpt_threads(int n, int ppb);
+long long tpt_blocks(long long npencils, int ppb);
+
+// ---- kernels.cu ---------------------------------------------------------------
+// y_f = scale (W (x) W) x_f for every face f (n x n nodes, lower axis fastest),
+// optionally y_f += ...;  nfaces faces per right-hand side, strides in values.
+template <typename TI, typename TO>
+cudaError_t launch_face_transform(int n, const TI* x, TO* y, long long nfaces, int nrhs,
+                                  long long stride_x, long long stride_y, const Mat1D<double>& W,
+                                  double scale, int accumulate, cudaStream_t s);
+
+// y_e = scale_e (A (x) A (x) A) x_e per element (n^3 values, x1 fastest);
+// scale_e = metric[4 e + 0] (d0) if use_d0, else 1.
+cudaError_t launch_volume_transform(int n, const double* x, double* y, long long nelem, int nrhs,
+                                    long long stride, const Mat1D<double>& A, const double* metric,
+                                    int uniform, int use_d0, cudaStream_t s);
+
+// D_Z^-1 tables: out[r][cls][i + n j + n^2 k] = 1 / (lam_r d0 + d1 L_i + d2 L_j + d3 L_k)
+template <typename T>
+cudaError_t launch_dinv(int n, const double* lambda_dev, int nrhs, const double* metric,
+                        long long nclass, const double* Lambda_dev, T* out, cudaStream_t s);
+
+// F-hat[unknown Neumann face] += (h_a h_b / 4) g-hat[boundary face]
+cudaError_t launch_neumann_add(const MeshDev& m, int n, const double* widths_dev /*3 x maxN*/,
+                               int wstride, const double* ghat, double* F, int nrhs,
+                               long long bstride, long long tstride, cudaStream_t s);
+
+// element-wise vector helpers over nrhs blocks of length len (stride = len)
+template <typename TI, typename TO>
+cudaError_t launch_convert(const TI* x, TO* y, long long count, cudaStream_t s);
+cudaError_t launch_sub(const double* a, const double* b, double* out, long long count, cudaStream_t s);  // out = a - b
+template <typename T>
+cudaError_t launch_add_to(double* x, const T* d, long long count, cudaStream_t s);  // x += d
+
+// deterministic dot products a_r . b_r per right-hand side into out[r]
+// (partials[nrhs * blocks], counter[nrhs] zero on entry and exit)
+template <typename T>
+cudaError_t launch_dot(const T* a, const T* b, long long len, int nrhs, double* partials,
+                       unsigned int* counter, double* out, int blocks, cudaStream_t s);
+
+// ---- CG (cg_kernels in kernels.cu) ----------------------------------------------
+struct CgScalars {
+  double rr;        // r . r of the current iterate
+  double rr_stop;   // stop when rr <= rr_stop
+  double alpha, beta;
+  int it, max_it;
+  int done;         // 1: stop (converged, iteration cap or breakdown)
+  int status;       // 0 ok / converged, 5 not converged, 6 breakdown
+};
+
+// init: rr from dot result, rr_stop = tol^2 rr, done if rr == 0 (or if the
+// right-hand side is already masked in `flags`); flags[r] mirrors done.
+cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, double tol, int max_it,
+                           int nrhs, cudaStream_t s);
+// alpha = rr / pq; d += alpha p; r -= alpha q; rr' = r.r; beta = rr'/rr; the
+// last block updates the scalars and flags[r] (no effect once done)
+template <typename T>
+cudaError_t launch_cg_update(CgScalars* cg, int* flags, const double* pq, T* d, T* r, const T* p,
+                             const T* q, long long len, int nrhs, double* partials,
+                             unsigned int* counter, int blocks, cudaStream_t s);
+// p = r + beta p (skips finished right-hand sides)
+template <typename T>
+cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, long long len, int nrhs,
+                              cudaStream_t s);
+
+}  // namespace hdg

@@ -1,0 +1,525 @@
+// Face and volume tensor-product transforms, D_Z^-1 tables, vector kernels
+// and the CG scalar updates of the condensed HDG library.
+#include <cfloat>
+
+#include "internal.h"
+
+namespace hdg {
+namespace {
+
+constexpr int kVecThreads = 256;
+
+inline unsigned int grid_for(long long count, int threads, long long cap = 152LL * 32) {
+  long long b = (count + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned int)b;
+}
+
+// ---- face transforms: y_f = scale (W (x) W) x_f (Sec. 4.2 basis change) ------
+template <typename TI, typename TO, int N>
+__global__ void face_transform_kernel(const TI* __restrict__ x, TO* __restrict__ y, long long nfaces,
+                                      long long sx, long long sy, const Mat1D<TO> W, TO scale,
+                                      int accumulate, int fpb) {
+  constexpr int N2 = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TO* sm = reinterpret_cast<TO*>(smem_raw);
+  const int slot = threadIdx.x / N2;
+  const int q = threadIdx.x - slot * N2;
+  const long long face = (long long)blockIdx.x * fpb + slot;
+  const bool act = slot < fpb && face < nfaces;
+  const int r = blockIdx.y;
+  TO* X = sm + (act ? slot : 0) * 2 * N2;
+  TO* Tm = X + N2;
+  const int a1 = q % N, a2 = q / N;
+  if (act) X[q] = load_as<TI, TO>(x + r * sx + face * N2 + q);
+  __syncthreads();
+  if (act) {
+    // T[c2][a1] = sum_c1 W[a1][c1] X[c2][c1]   (q = a1 + N c2)
+    TO t = TO(0);
+#pragma unroll
+    for (int c1 = 0; c1 < N; ++c1) t = fma(W.a[a1 * N + c1], X[a2 * N + c1], t);
+    Tm[q] = t;
+  }
+  __syncthreads();
+  if (act) {
+    // Y[a2][a1] = sum_c2 W[a2][c2] T[c2][a1]
+    TO v = TO(0);
+#pragma unroll
+    for (int c2 = 0; c2 < N; ++c2) v = fma(W.a[a2 * N + c2], Tm[c2 * N + a1], v);
+    v *= scale;
+    TO* dst = y + r * sy + face * N2 + q;
+    if (accumulate) v += *dst;
+    *dst = v;
+  }
+}
+
+// ---- volume transforms: y_e = s_e (A (x) A (x) A) x_e -------------------------
+template <int N>
+__global__ void volume_transform_kernel(const double* __restrict__ x, double* __restrict__ y,
+                                        long long nelem, long long stride, const Mat1D<double> A,
+                                        const double* __restrict__ metric, int uniform, int use_d0,
+                                        int epb) {
+  constexpr int N2 = N * N, N3 = N2 * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  const int slot = threadIdx.x / N2;
+  const int q = threadIdx.x - slot * N2;
+  const long long e = (long long)blockIdx.x * epb + slot;
+  const bool act = slot < epb && e < nelem;
+  const int r = blockIdx.y;
+  double* B0 = sm + (act ? slot : 0) * 2 * N3;
+  double* B1 = B0 + N3;
+  const double* xe = x + r * stride + e * N3;
+  const int lo = q % N, hi = q / N;
+  if (act) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) B0[q + N2 * t] = xe[q + N2 * t];
+  }
+  __syncthreads();
+  // pass 1 (x1): B1[k][j][a] = sum_i A[a][i] B0[k][j][i]; thread (j, k) = (lo, hi)
+  if (act) {
+    double in[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) in[i] = B0[i + N * lo + N2 * hi];
+#pragma unroll
+    for (int aa = 0; aa < N; ++aa) {
+      double v = 0.0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) v = fma(A.a[aa * N + i], in[i], v);
+      B1[aa + N * lo + N2 * hi] = v;
+    }
+  }
+  __syncthreads();
+  // pass 2 (x2): B0[k][b][i] = sum_j A[b][j] B1[k][j][i]; thread (i, k) = (lo, hi)
+  if (act) {
+    double in[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) in[j] = B1[lo + N * j + N2 * hi];
+#pragma unroll
+    for (int bb = 0; bb < N; ++bb) {
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < N; ++j) v = fma(A.a[bb * N + j], in[j], v);
+      B0[lo + N * bb + N2 * hi] = v;
+    }
+  }
+  __syncthreads();
+  // pass 3 (x3): y[c][j][i] = s sum_k A[c][k] B0[k][j][i]; thread (i, j) = (lo, hi)
+  if (act) {
+    const double s = use_d0 ? metric[uniform ? 0 : 4 * e] : 1.0;
+    double in[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) in[k] = B0[lo + N * hi + N2 * k];
+    double* ye = y + r * stride + e * N3;
+#pragma unroll
+    for (int cc = 0; cc < N; ++cc) {
+      double v = 0.0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) v = fma(A.a[cc * N + k], in[k], v);
+      ye[lo + N * hi + N2 * cc] = s * v;
+    }
+  }
+}
+
+// ---- D_Z^-1 tables (Sec. 4.1, fast diagonalisation) -------------------------------
+template <typename T>
+__global__ void dinv_kernel(int n, const double* __restrict__ lam, int nrhs,
+                            const double* __restrict__ metric, long long nclass,
+                            const double* __restrict__ Lambda, T* __restrict__ out) {
+  const long long n3 = (long long)n * n * n;
+  const long long total = (long long)nrhs * nclass * n3;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long p = t % n3;
+    const long long cls = (t / n3) % nclass;
+    const int r = (int)(t / (n3 * nclass));
+    const int i = (int)(p % n), j = (int)((p / n) % n), k = (int)(p / (n * n));
+    const double* mt = metric + 4 * cls;
+    const double dz = lam[r] * mt[0] + mt[1] * Lambda[i] + mt[2] * Lambda[j] + mt[3] * Lambda[k];
+    out[t] = static_cast<T>(1.0 / dz);
+  }
+}
+
+// ---- Neumann load in the transformed basis -------------------------------------
+__global__ void neumann_add_kernel(MeshDev m, int n, const double* __restrict__ widths, int wstride,
+                                   const double* __restrict__ ghat, double* __restrict__ F,
+                                   long long bstride, long long tstride) {
+  const int r = blockIdx.y;
+  const long long n2 = (long long)n * n;
+  const long long total = m.nbfaces * n2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long bf = t / n2, node = t % n2;
+    int side = 5;
+    while (side > 0 && bf < m.side[side]) --side;
+    const int d = side / 2, s = side % 2;
+    const int plane = s == 0 ? 0 : m.ne[d];
+    if (plane < m.lo[d] || plane > m.hi[d]) continue;   // Dirichlet side
+    const int ax = d == 0 ? 1 : 0, bx = d == 2 ? 1 : 2;
+    const long long ab = bf - m.side[side];
+    const int Na = m.ne[ax];
+    const int ea = (int)(ab % Na), eb = (int)(ab / Na);
+    const double scale = widths[ax * wstride + ea] * widths[bx * wstride + eb] * 0.25;
+    const long long Na_Nb = (long long)Na * m.ne[bx];
+    const long long uf = m.blk[d] + (long long)(plane - m.lo[d]) * Na_Nb + ab;
+    F[r * tstride + uf * n2 + node] += scale * ghat[r * bstride + t];
+  }
+}
+
+// ---- element-wise helpers ----------------------------------------------------------
+template <typename TI, typename TO>
+__global__ void convert_kernel(const TI* __restrict__ x, TO* __restrict__ y, long long count) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+       t += (long long)gridDim.x * blockDim.x)
+    store_from<TO, TO>(y + t, static_cast<TO>(load_as<TI, double>(x + t)));
+}
+template <>
+__global__ void convert_kernel<double, __nv_bfloat16>(const double* __restrict__ x,
+                                                      __nv_bfloat16* __restrict__ y, long long count) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+       t += (long long)gridDim.x * blockDim.x)
+    y[t] = __double2bfloat16(x[t]);
+}
+
+__global__ void sub_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ out, long long count) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = a[t] - b[t];
+}
+
+template <typename T>
+__global__ void add_to_kernel(double* __restrict__ x, const T* __restrict__ d, long long count) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+       t += (long long)gridDim.x * blockDim.x)
+    x[t] += static_cast<double>(d[t]);
+}
+
+// block sum of a double, result valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) ws[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x + 31) / 32; ++i) s += ws[i];
+  return s;
+}
+
+// Writes the block partial; returns true in thread 0 of the last block to
+// finish, after which every partial of right-hand side r is visible.
+__device__ __forceinline__ bool finish_partial(double s, double* partials, unsigned int* counter, int r) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    partials[(long long)r * gridDim.x + blockIdx.x] = s;
+    __threadfence();
+    const unsigned int done = atomicAdd(counter + r, 1u);
+    last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ double sum_partials(const double* partials, int r) {
+  const volatile double* pp = partials + (long long)r * gridDim.x;
+  double s = 0.0;
+  for (unsigned int b = 0; b < gridDim.x; ++b) s += pp[b];
+  return s;
+}
+
+template <typename T>
+__global__ void dot_kernel(const T* __restrict__ a, const T* __restrict__ b, long long len,
+                           double* partials, unsigned int* counter, double* out) {
+  const int r = blockIdx.y;
+  const T* ar = a + r * len;
+  const T* br = b + r * len;
+  double acc = 0.0;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+       t += (long long)gridDim.x * blockDim.x)
+    acc += static_cast<double>(ar[t]) * static_cast<double>(br[t]);
+  const double s = block_sum(acc);
+  if (finish_partial(s, partials, counter, r)) {
+    out[r] = sum_partials(partials, r);
+    counter[r] = 0u;
+  }
+}
+
+// FP32 dot: accumulate in FP32 per thread (no FP64 arithmetic in the loop)
+template <>
+__global__ void dot_kernel<float>(const float* __restrict__ a, const float* __restrict__ b,
+                                  long long len, double* partials, unsigned int* counter, double* out) {
+  const int r = blockIdx.y;
+  const float* ar = a + r * len;
+  const float* br = b + r * len;
+  float acc = 0.f;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+       t += (long long)gridDim.x * blockDim.x)
+    acc = fmaf(ar[t], br[t], acc);
+  const double s = block_sum((double)acc);
+  if (finish_partial(s, partials, counter, r)) {
+    out[r] = sum_partials(partials, r);
+    counter[r] = 0u;
+  }
+}
+
+// ---- CG scalars ----------------------------------------------------------------------
+__global__ void cg_init_kernel(CgScalars* cg, int* flags, const double* rr, double tol, int max_it,
+                               int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  CgScalars c;
+  c.rr = rr[r];
+  c.rr_stop = tol * tol * c.rr;
+  c.alpha = 0.0;
+  c.beta = 0.0;
+  c.it = 0;
+  c.max_it = max_it;
+  c.status = 0;
+  c.done = (flags[r] != 0) || !(c.rr > 0.0) || max_it <= 0;
+  if (!(c.rr >= 0.0) || c.rr != c.rr) c.status = 6;
+  cg[r] = c;
+  flags[r] = c.done;
+}
+
+template <typename T>
+__global__ void cg_update_kernel(CgScalars* cg, int* flags, const double* __restrict__ pq,
+                                 T* __restrict__ d, T* __restrict__ rvec, const T* __restrict__ p,
+                                 const T* __restrict__ q, long long len, double* partials,
+                                 unsigned int* counter) {
+  const int r = blockIdx.y;
+  if (flags[r]) return;
+  // scalars once per block: FP64 division is slow on this part
+  __shared__ double s_alpha;
+  __shared__ bool s_bad;
+  __shared__ T s_al;
+  const double rr = cg[r].rr;
+  if (threadIdx.x == 0) {
+    const double pqv = pq[r];
+    s_bad = !(pqv > 0.0) || !(rr == rr) || !(pqv == pqv) || pqv > DBL_MAX;
+    s_alpha = s_bad ? 0.0 : rr / pqv;
+    s_al = static_cast<T>(s_alpha);
+  }
+  __syncthreads();
+  const bool bad = s_bad;
+  const double alpha = s_alpha;
+  const T al = s_al;
+  T* dr = d + r * len;
+  T* rv = rvec + r * len;
+  const T* pr = p + r * len;
+  const T* qr = q + r * len;
+  T acc = T(0);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+       t += (long long)gridDim.x * blockDim.x) {
+    dr[t] = fma(al, pr[t], dr[t]);
+    const T rn = fma(-al, qr[t], rv[t]);
+    rv[t] = rn;
+    acc = fma(rn, rn, acc);
+  }
+  const double s = block_sum(static_cast<double>(acc));
+  if (finish_partial(s, partials, counter, r)) {
+    const double rr_new = sum_partials(partials, r);
+    counter[r] = 0u;
+    CgScalars c = cg[r];
+    c.alpha = alpha;
+    c.it += 1;
+    if (bad || !(rr_new == rr_new)) {
+      c.status = 6;
+      c.done = 1;
+    } else {
+      c.beta = rr_new / rr;
+      c.rr = rr_new;
+      if (rr_new <= c.rr_stop) c.done = 1;
+      else if (c.it >= c.max_it) { c.done = 1; c.status = 5; }
+    }
+    cg[r] = c;
+    flags[r] = c.done;
+  }
+}
+
+template <typename T>
+__global__ void cg_pupdate_kernel(const CgScalars* cg, T* __restrict__ p, const T* __restrict__ rvec,
+                                  long long len) {
+  const int r = blockIdx.y;
+  if (cg[r].done) return;
+  __shared__ T s_beta;
+  if (threadIdx.x == 0) s_beta = static_cast<T>(cg[r].beta);
+  __syncthreads();
+  const T beta = s_beta;
+  T* pr = p + r * len;
+  const T* rr = rvec + r * len;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
+       t += (long long)gridDim.x * blockDim.x)
+    pr[t] = fma(beta, pr[t], rr[t]);
+}
+
+template <typename TI, typename TO, int N>
+cudaError_t ft_one(const TI* x, TO* y, long long nfaces, int nrhs, long long sx, long long sy,
+                   const Mat1D<double>& Wd, double scale, int accumulate, cudaStream_t s) {
+  Mat1D<TO> W;
+  for (int i = 0; i < N * N; ++i) W.a[i] = static_cast<TO>(Wd.a[i]);
+  const int fpb = (256 / (N * N)) > 0 ? 256 / (N * N) : 1;
+  const int threads = (fpb * N * N + 31) / 32 * 32;
+  const size_t smem = (size_t)fpb * 2 * N * N * sizeof(TO);
+  dim3 grid((unsigned)((nfaces + fpb - 1) / fpb), nrhs);
+  if (nfaces <= 0) return cudaSuccess;
+  face_transform_kernel<TI, TO, N><<<grid, threads, smem, s>>>(x, y, nfaces, sx, sy, W,
+                                                               static_cast<TO>(scale), accumulate, fpb);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t vt_one(const double* x, double* y, long long nelem, int nrhs, long long stride,
+                   const Mat1D<double>& A, const double* metric, int uniform, int use_d0,
+                   cudaStream_t s) {
+  const int epb = (256 / (N * N)) > 0 ? 256 / (N * N) : 1;
+  const int threads = (epb * N * N + 31) / 32 * 32;
+  const size_t smem = (size_t)epb * 2 * N * N * N * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(volume_transform_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)((nelem + epb - 1) / epb), nrhs);
+  if (nelem <= 0) return cudaSuccess;
+  volume_transform_kernel<N><<<grid, threads, smem, s>>>(x, y, nelem, stride, A, metric, uniform,
+                                                        use_d0, epb);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+#define HDG_N_SWITCH(n, CALL)                                                   \
+  switch (n) {                                                                  \
+    case 2: return CALL(2); case 3: return CALL(3); case 4: return CALL(4);     \
+    case 5: return CALL(5); case 6: return CALL(6); case 7: return CALL(7);     \
+    case 8: return CALL(8); case 9: return CALL(9); case 10: return CALL(10);   \
+    case 11: return CALL(11); case 12: return CALL(12); case 13: return CALL(13); \
+    case 14: return CALL(14); case 15: return CALL(15); case 16: return CALL(16); \
+    case 17: return CALL(17);                                                   \
+    default: return cudaErrorInvalidValue;                                      \
+  }
+
+template <typename TI, typename TO>
+cudaError_t launch_face_transform(int n, const TI* x, TO* y, long long nfaces, int nrhs,
+                                  long long stride_x, long long stride_y, const Mat1D<double>& W,
+                                  double scale, int accumulate, cudaStream_t s) {
+#define FT_CALL(N) ft_one<TI, TO, N>(x, y, nfaces, nrhs, stride_x, stride_y, W, scale, accumulate, s)
+  HDG_N_SWITCH(n, FT_CALL)
+#undef FT_CALL
+}
+template cudaError_t launch_face_transform<double, double>(int, const double*, double*, long long, int,
+                                                           long long, long long, const Mat1D<double>&,
+                                                           double, int, cudaStream_t);
+template cudaError_t launch_face_transform<float, float>(int, const float*, float*, long long, int,
+                                                         long long, long long, const Mat1D<double>&,
+                                                         double, int, cudaStream_t);
+
+cudaError_t launch_volume_transform(int n, const double* x, double* y, long long nelem, int nrhs,
+                                    long long stride, const Mat1D<double>& A, const double* metric,
+                                    int uniform, int use_d0, cudaStream_t s) {
+#define VT_CALL(N) vt_one<N>(x, y, nelem, nrhs, stride, A, metric, uniform, use_d0, s)
+  HDG_N_SWITCH(n, VT_CALL)
+#undef VT_CALL
+}
+
+template <typename T>
+cudaError_t launch_dinv(int n, const double* lambda_dev, int nrhs, const double* metric,
+                        long long nclass, const double* Lambda_dev, T* out, cudaStream_t s) {
+  const long long total = (long long)nrhs * nclass * n * n * n;
+  dinv_kernel<T><<<grid_for(total, kVecThreads), kVecThreads, 0, s>>>(n, lambda_dev, nrhs, metric,
+                                                                      nclass, Lambda_dev, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dinv<double>(int, const double*, int, const double*, long long,
+                                         const double*, double*, cudaStream_t);
+template cudaError_t launch_dinv<float>(int, const double*, int, const double*, long long,
+                                        const double*, float*, cudaStream_t);
+
+cudaError_t launch_neumann_add(const MeshDev& m, int n, const double* widths_dev, int wstride,
+                               const double* ghat, double* F, int nrhs, long long bstride,
+                               long long tstride, cudaStream_t s) {
+  const long long total = m.nbfaces * n * n;
+  dim3 grid(grid_for(total, kVecThreads), nrhs);
+  neumann_add_kernel<<<grid, kVecThreads, 0, s>>>(m, n, widths_dev, wstride, ghat, F, bstride, tstride);
+  return cudaGetLastError();
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_convert(const TI* x, TO* y, long long count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  convert_kernel<TI, TO><<<grid_for(count, kVecThreads), kVecThreads, 0, s>>>(x, y, count);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<double, float>(const double*, float*, long long, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, double>(const double*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert<double, __nv_bfloat16>(const double*, __nv_bfloat16*, long long,
+                                                          cudaStream_t);
+
+cudaError_t launch_sub(const double* a, const double* b, double* out, long long count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  sub_kernel<<<grid_for(count, kVecThreads), kVecThreads, 0, s>>>(a, b, out, count);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_add_to(double* x, const T* d, long long count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  add_to_kernel<T><<<grid_for(count, kVecThreads), kVecThreads, 0, s>>>(x, d, count);
+  return cudaGetLastError();
+}
+template cudaError_t launch_add_to<double>(double*, const double*, long long, cudaStream_t);
+template cudaError_t launch_add_to<float>(double*, const float*, long long, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_dot(const T* a, const T* b, long long len, int nrhs, double* partials,
+                       unsigned int* counter, double* out, int blocks, cudaStream_t s) {
+  dim3 grid(blocks, nrhs);
+  dot_kernel<T><<<grid, kVecThreads, 0, s>>>(a, b, len, partials, counter, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dot<double>(const double*, const double*, long long, int, double*,
+                                        unsigned int*, double*, int, cudaStream_t);
+template cudaError_t launch_dot<float>(const float*, const float*, long long, int, double*,
+                                       unsigned int*, double*, int, cudaStream_t);
+
+cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, double tol, int max_it,
+                           int nrhs, cudaStream_t s) {
+  cg_init_kernel<<<(nrhs + 127) / 128, 128, 0, s>>>(cg, flags, rr, tol, max_it, nrhs);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cg_update(CgScalars* cg, int* flags, const double* pq, T* d, T* r, const T* p,
+                             const T* q, long long len, int nrhs, double* partials,
+                             unsigned int* counter, int blocks, cudaStream_t s) {
+  dim3 grid(blocks, nrhs);
+  cg_update_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, pq, d, r, p, q, len, partials, counter);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cg_update<double>(CgScalars*, int*, const double*, double*, double*,
+                                              const double*, const double*, long long, int, double*,
+                                              unsigned int*, int, cudaStream_t);
+template cudaError_t launch_cg_update<float>(CgScalars*, int*, const double*, float*, float*,
+                                             const float*, const float*, long long, int, double*,
+                                             unsigned int*, int, cudaStream_t);
+
+template <typename T>
+cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, long long len, int nrhs,
+                              cudaStream_t s) {
+  dim3 grid(grid_for(len, kVecThreads), nrhs);
+  cg_pupdate_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, p, r, len);
+  return cudaGetLastError();
+}
+template cudaError_t launch_cg_pupdate<double>(const CgScalars*, double*, const double*, long long,
+                                               int, cudaStream_t);
+template cudaError_t launch_cg_pupdate<float>(const CgScalars*, float*, const float*, long long, int,
+                                              cudaStream_t);
+
+}  // namespace hdg

@@ -1,0 +1,58 @@
+// Launch helpers for tpt_kernel: one translation unit per precision includes
+// this file and instantiates launch_tpt<T, ST> for n = 2..17.
+#pragma once
+
+#include "internal.h"
+
+namespace hdg {
+
+template <typename T, typename ST, int N, int MODE>
+cudaError_t tpt_launch_one(const TptArgs<T, ST>& a, int nrhs, cudaStream_t s) {
+  if (a.npencils <= 0) return cudaSuccess;
+  const int threads = tpt_threads(N, a.ppb);
+  const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<N>() * sizeof(T);
+  if (threads > 512) return cudaErrorInvalidConfiguration;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(tpt_kernel<T, ST, N, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)tpt_blocks(a.npencils, a.ppb), (unsigned)nrhs);
+  tpt_kernel<T, ST, N, MODE><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, typename ST, int N>
+cudaError_t tpt_launch_mode(int mode, const TptArgs<T, ST>& a, int nrhs, cudaStream_t s) {
+  switch (mode) {
+    case TPT_APPLY: return tpt_launch_one<T, ST, N, TPT_APPLY>(a, nrhs, s);
+    case TPT_RHS: return tpt_launch_one<T, ST, N, TPT_RHS>(a, nrhs, s);
+    case TPT_RECOVER: return tpt_launch_one<T, ST, N, TPT_RECOVER>(a, nrhs, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, typename ST>
+cudaError_t tpt_dispatch(int mode, int n, const TptArgs<T, ST>& a, int nrhs, cudaStream_t s) {
+  switch (n) {
+    case 2: return tpt_launch_mode<T, ST, 2>(mode, a, nrhs, s);
+    case 3: return tpt_launch_mode<T, ST, 3>(mode, a, nrhs, s);
+    case 4: return tpt_launch_mode<T, ST, 4>(mode, a, nrhs, s);
+    case 5: return tpt_launch_mode<T, ST, 5>(mode, a, nrhs, s);
+    case 6: return tpt_launch_mode<T, ST, 6>(mode, a, nrhs, s);
+    case 7: return tpt_launch_mode<T, ST, 7>(mode, a, nrhs, s);
+    case 8: return tpt_launch_mode<T, ST, 8>(mode, a, nrhs, s);
+    case 9: return tpt_launch_mode<T, ST, 9>(mode, a, nrhs, s);
+    case 10: return tpt_launch_mode<T, ST, 10>(mode, a, nrhs, s);
+    case 11: return tpt_launch_mode<T, ST, 11>(mode, a, nrhs, s);
+    case 12: return tpt_launch_mode<T, ST, 12>(mode, a, nrhs, s);
+    case 13: return tpt_launch_mode<T, ST, 13>(mode, a, nrhs, s);
+    case 14: return tpt_launch_mode<T, ST, 14>(mode, a, nrhs, s);
+    case 15: return tpt_launch_mode<T, ST, 15>(mode, a, nrhs, s);
+    case 16: return tpt_launch_mode<T, ST, 16>(mode, a, nrhs, s);
+    case 17: return tpt_launch_mode<T, ST, 17>(mode, a, nrhs, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace hdg

@@ -1,0 +1,175 @@
+"""Torch-facing wrapper of the C ABI (device memory and streams from torch).
+
+Every operation runs in the CUDA library; this module only checks shapes and
+dtypes, passes ``data_ptr()`` values and the current torch stream, and
+raises on a non-OK status.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _capi
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _lams(lam, nrhs):
+    if isinstance(lam, torch.Tensor):
+        lam = lam.detach().cpu().reshape(-1).tolist()
+    elif np.isscalar(lam):
+        lam = [float(lam)] * nrhs
+    lam = [float(v) for v in lam]
+    if len(lam) != nrhs:
+        raise ValueError("need one lambda per right-hand side")
+    return _capi.doubles(lam)
+
+
+class HDG:
+    """One Cartesian mesh + degree + penalty on the current CUDA device.
+
+    ne: elements per direction; grid: three increasing coordinate arrays of
+    length ne[d] + 1; bc: six sides (x1-, x1+, x2-, x2+, x3-, x3+), 0 for
+    Dirichlet and 1 for Neumann; p: degree 1..16; tau_hat: penalty
+    (tau_{i,e} = 2 tau_hat / h_{i,e}).
+    """
+
+    def __init__(self, ne, grid, bc=(0, 0, 0, 0, 0, 0), p=4, tau_hat=25.0, mass_lumped=False):
+        L = _capi.lib()
+        torch.cuda.init()
+        self.ne = tuple(int(v) for v in ne)
+        self.p, self.n = int(p), int(p) + 1
+        self.bc = tuple(int(v) for v in bc)
+        self._grid = [(ctypes.c_double * (self.ne[d] + 1))(*[float(v) for v in grid[d]]) for d in range(3)]
+        m = _capi.HdgMesh()
+        for d in range(3):
+            m.ne[d] = self.ne[d]
+            m.h_grid[d] = ctypes.cast(self._grid[d], ctypes.POINTER(ctypes.c_double))
+        for s in range(6):
+            m.bc[s] = self.bc[s]
+        o = _capi.HdgOptions(float(tau_hat), int(bool(mass_lumped)))
+        h = ctypes.c_void_p()
+        _capi.check(L.hdg_setup(ctypes.byref(m), self.p, ctypes.byref(o), ctypes.byref(h)), "hdg_setup")
+        self._h = h
+        self.trace_size = int(L.hdg_trace_size(h))
+        self.volume_size = int(L.hdg_volume_size(h))
+        self.boundary_size = int(L.hdg_boundary_size(h))
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _capi.lib().hdg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- measurement -------------------------------------------------------------
+    KERNEL_CLASSES = {"op_fp32": 0, "op_fp64": 1, "face": 2, "volume": 3, "rhs_recover": 4, "vector": 5}
+
+    def profile(self, enable):
+        """Start (reset) or stop per-launch event timing inside the library."""
+        _capi.check(_capi.lib().hdg_profile(self._h, int(bool(enable))), "hdg_profile")
+
+    def profile_read(self, kernel_class):
+        """(total ms, launches) of one kernel class; "all" gives (0, launches
+        of every class since profile(True))."""
+        cls = -1 if kernel_class == "all" else self.KERNEL_CLASSES[kernel_class]
+        ms, cnt = ctypes.c_double(), ctypes.c_longlong()
+        _capi.check(_capi.lib().hdg_profile_read(self._h, cls, ctypes.byref(ms), ctypes.byref(cnt)),
+                    "hdg_profile_read")
+        return ms.value, cnt.value
+
+    def nodes(self):
+        out = (ctypes.c_double * self.n)()
+        _capi.check(_capi.lib().hdg_get_nodes(self._h, out), "hdg_get_nodes")
+        return np.array(out[:])
+
+    # -- operator ------------------------------------------------------------
+    def apply(self, x, lam, basis="nodal", out=None):
+        """y = K x (homogeneous Dirichlet data).  x: (T,) or (nrhs, T) CUDA
+        tensor, float64 or float32 (the precision of the application)."""
+        x2 = x.reshape(-1, self.trace_size)
+        if not x2.is_cuda or not x2.is_contiguous():
+            raise ValueError("x must be a contiguous CUDA tensor")
+        prec = {torch.float64: "fp64", torch.float32: "fp32", torch.bfloat16: "bf16"}[x2.dtype]
+        y = torch.empty_like(x2) if out is None else out.reshape(-1, self.trace_size)
+        nrhs = x2.shape[0]
+        st = _capi.lib().hdg_apply(self._h, nrhs, _lams(lam, nrhs), _capi.PRECISION[prec],
+                                   _capi.BASIS[basis], ctypes.c_void_p(x2.data_ptr()),
+                                   ctypes.c_void_p(y.data_ptr()), _stream())
+        _capi.check(st, "hdg_apply")
+        return y.reshape(x.shape)
+
+    # -- solve -----------------------------------------------------------------
+    def _opts(self, tol, inner, max_iter, max_outer, inner_tol):
+        return _capi.HdgSolveOpts(float(tol), int(max_iter), int(max_outer), _capi.PRECISION[inner],
+                                  float(inner_tol))
+
+    def solve(self, f, lam, bdry=None, x0=None, tol=1e-10, inner="fp32", max_iter=50000,
+              max_outer=40, inner_tol=0.0, return_u=True, check=True):
+        """Solve K ut = F for nodal loads f ((V,) or (nrhs, V), float64).
+        Returns (traces, u or None, list of info dicts)."""
+        f2 = f.reshape(-1, self.volume_size).contiguous()
+        nrhs = f2.shape[0]
+        if f2.dtype != torch.float64 or not f2.is_cuda:
+            raise ValueError("f must be a float64 CUDA tensor")
+        tr = torch.empty((nrhs, self.trace_size), dtype=torch.float64, device=f2.device)
+        u = torch.empty_like(f2) if return_u else None
+        b = None if bdry is None else bdry.reshape(nrhs, self.boundary_size).contiguous()
+        x = None if x0 is None else x0.reshape(nrhs, self.trace_size).contiguous()
+        info = (_capi.HdgSolveInfo * nrhs)()
+        opts = self._opts(tol, inner, max_iter, max_outer, inner_tol)
+        st = _capi.lib().hdg_solve(self._h, nrhs, _lams(lam, nrhs), ctypes.c_void_p(f2.data_ptr()),
+                                   ctypes.c_void_p(b.data_ptr() if b is not None else 0),
+                                   ctypes.c_void_p(x.data_ptr() if x is not None else 0),
+                                   ctypes.c_void_p(tr.data_ptr()),
+                                   ctypes.c_void_p(u.data_ptr() if u is not None else 0),
+                                   ctypes.byref(opts), info, _stream())
+        infos = [info[i].as_dict() for i in range(nrhs)]
+        if check:
+            _capi.check(st, "hdg_solve")
+        shape_t = (self.trace_size,) if f.dim() == 1 else (nrhs, self.trace_size)
+        return tr.reshape(shape_t), (u.reshape(f.shape) if u is not None else None), infos
+
+    def solve_adjoint(self, u, grad_u, lam, tol=1e-10, inner="fp32", max_iter=50000, max_outer=40,
+                      inner_tol=0.0):
+        """dL/df and dL/dlambda for dL/du = grad_u at the forward solution u
+        (homogeneous boundary data)."""
+        u2 = u.reshape(-1, self.volume_size).contiguous()
+        g2 = grad_u.reshape(-1, self.volume_size).contiguous().to(torch.float64)
+        nrhs = u2.shape[0]
+        gf = torch.empty_like(u2)
+        gl = torch.empty(nrhs, dtype=torch.float64, device=u2.device)
+        info = (_capi.HdgSolveInfo * nrhs)()
+        opts = self._opts(tol, inner, max_iter, max_outer, inner_tol)
+        st = _capi.lib().hdg_solve_adjoint(self._h, nrhs, _lams(lam, nrhs), ctypes.c_void_p(u2.data_ptr()),
+                                           ctypes.c_void_p(g2.data_ptr()), ctypes.c_void_p(gf.data_ptr()),
+                                           ctypes.c_void_p(gl.data_ptr()), ctypes.byref(opts), info, _stream())
+        _capi.check(st, "hdg_solve_adjoint")
+        return gf.reshape(u.shape), gl, [info[i].as_dict() for i in range(nrhs)]
+
+
+class HDGSolve(torch.autograd.Function):
+    """u = solve(f, lambda) with homogeneous boundary data; backward runs the
+    hand-written adjoint solve (dL/df = M z_u, dL/dlambda = -z_u^T M u)."""
+
+    @staticmethod
+    def forward(ctx, f, lam, hdg, tol=1e-10, inner="fp32"):
+        lam_list = lam.detach().reshape(-1).tolist()
+        _, u, _ = hdg.solve(f.detach(), lam_list, tol=tol, inner=inner)
+        ctx.hdg, ctx.tol, ctx.inner, ctx.lam = hdg, tol, inner, lam_list
+        ctx.save_for_backward(u)
+        ctx.lam_shape = lam.shape
+        return u
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (u,) = ctx.saved_tensors
+        gf, gl, _ = ctx.hdg.solve_adjoint(u, grad_u.contiguous(), ctx.lam, tol=ctx.tol, inner=ctx.inner)
+        return gf, gl.reshape(ctx.lam_shape), None, None, None

@@ -1,0 +1,133 @@
+"""GPU parity of the condensed operator K (hdg_apply) against the CPU oracle.
+
+The FP64 apply must match the oracle's dense-condensed global apply within
+1e-12 relative (max-norm); the FP32 apply within 1e-5.  Meshes span several
+CTAs with ragged tails, stretched grids, mixed Dirichlet/Neumann sides,
+single-element directions, and degrees 1..16.  At the full sizes of the
+16^3 stretched p = 8 and 32^3 uniform p = 8 workloads, sampled outputs are
+compared with the oracle's per-face evaluation.
+"""
+import numpy as np
+import pytest
+import torch
+
+import hdg_inputs
+from oracle.solver import Problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2007_11891_gb300 import build
+    build.build(verbose=False)
+
+
+def _grid(ne, stretched, seed):
+    rng = np.random.default_rng(seed)
+    out = []
+    for d in range(3):
+        w = rng.uniform(0.5, 2.0, ne[d]) if stretched else np.ones(ne[d])
+        x = np.concatenate([[0.0], np.cumsum(w)])
+        out.append(0.3 + 1.7 * x / x[-1])
+    return out
+
+
+CASES = [
+    # name, ne, bc, p, stretched, lam, tau_hat
+    ("single_neumann", (1, 1, 1), (1, 1, 1, 1, 1, 1), 2, False, 0.5, 25.0),
+    ("ragged_p3", (5, 7, 3), (0, 0, 0, 0, 0, 0), 3, True, 1.3, 25.0),
+    ("mixed_p1", (3, 2, 4), (1, 0, 0, 1, 1, 0), 1, True, 0.0, 10.0),
+    ("many_pencils_p2", (2, 9, 7), (0, 0, 0, 0, 0, 0), 2, False, 1.0, 25.0),
+    ("neumann_hi_p4", (4, 3, 3), (0, 1, 0, 1, 0, 1), 4, True, 2.0, 1.0),
+    ("p8_small", (3, 2, 2), (0, 1, 0, 0, 0, 1), 8, True, 10.0, 25.0),
+    ("p12_line", (3, 1, 1), (1, 0, 0, 0, 0, 0), 12, False, 1.0, 25.0),
+    ("p16_small", (2, 1, 2), (0, 0, 1, 0, 0, 0), 16, False, 1.0, 25.0),
+]
+
+
+def _pair(ne, bc, p, stretched, lam, tau, seed=0):
+    from paper_2007_11891_gb300 import HDG
+    grid = _grid(ne, stretched, seed)
+    return HDG(ne, grid, bc, p, tau), Problem(ne, grid, bc, p, tau, lam)
+
+
+@pytest.mark.parametrize("name,ne,bc,p,stretched,lam,tau", CASES, ids=[c[0] for c in CASES])
+def test_apply_fp64_matches_oracle(name, ne, bc, p, stretched, lam, tau):
+    h, pr = _pair(ne, bc, p, stretched, lam, tau)
+    assert h.trace_size == pr.mesh.n_trace
+    if h.trace_size == 0:
+        return
+    x = hdg_inputs.uniform_pm1(h.trace_size, 11893)
+    y = h.apply(torch.tensor(x, device="cuda"), lam).cpu().numpy()
+    ref = pr.apply(x)
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name,ne,bc,p,stretched,lam,tau", CASES[1:6], ids=[c[0] for c in CASES[1:6]])
+def test_apply_fp32_matches_oracle(name, ne, bc, p, stretched, lam, tau):
+    h, pr = _pair(ne, bc, p, stretched, lam, tau)
+    x = hdg_inputs.uniform_pm1(h.trace_size, 5)
+    y = h.apply(torch.tensor(x, device="cuda", dtype=torch.float32), lam).double().cpu().numpy()
+    ref = pr.apply(x)
+    assert np.abs(y - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_apply_batched_lambdas():
+    ne, bc, p = (3, 4, 2), (0, 0, 1, 0, 0, 0), 3
+    lams = [0.1, 1.0, 100.0, 0.0]
+    from paper_2007_11891_gb300 import HDG
+    grid = _grid(ne, True, 3)
+    h = HDG(ne, grid, bc, p, 25.0)
+    X = np.stack([hdg_inputs.uniform_pm1(h.trace_size, 20 + r) for r in range(len(lams))])
+    Y = h.apply(torch.tensor(X, device="cuda"), lams).cpu().numpy()
+    for r, lam in enumerate(lams):
+        ref = Problem(ne, grid, bc, p, 25.0, lam).apply(X[r])
+        assert np.abs(Y[r] - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_apply_is_deterministic_and_symmetric():
+    from paper_2007_11891_gb300 import HDG
+    ne, p = (6, 5, 4), 5
+    h = HDG(ne, _grid(ne, True, 9), (0, 1, 0, 0, 1, 0), p, 25.0)
+    a = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 1), device="cuda")
+    b = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 2), device="cuda")
+    for basis in ("nodal", "transformed"):
+        y1 = h.apply(a, 0.7, basis=basis)
+        y2 = h.apply(a, 0.7, basis=basis)
+        assert torch.equal(y1, y2)
+        # symmetry: b^T K a == a^T K b
+        ab = float(torch.dot(b, y1))
+        ba = float(torch.dot(a, h.apply(b, 0.7, basis=basis)))
+        assert abs(ab - ba) <= 1e-12 * max(abs(ab), 1.0)
+    # positive definiteness in the transformed basis (Dirichlet sides present)
+    assert float(torch.dot(a, h.apply(a, 0.0, basis="transformed"))) > 0
+
+
+def test_zero_in_zero_out_and_single_element_dirichlet():
+    from paper_2007_11891_gb300 import HDG
+    h = HDG((1, 1, 1), _grid((1, 1, 1), False, 0), (0,) * 6, 3, 25.0)
+    assert h.trace_size == 0
+    ne = (4, 4, 4)
+    h = HDG(ne, _grid(ne, False, 0), (0,) * 6, 4, 25.0)
+    z = torch.zeros(h.trace_size, dtype=torch.float64, device="cuda")
+    assert torch.count_nonzero(h.apply(z, 1.0)) == 0
+
+
+@pytest.mark.parametrize("workload", ["stretched_p8", "uniform32"])
+def test_apply_full_size_sampled(workload):
+    from paper_2007_11891_gb300 import HDG
+    cfg = hdg_inputs.WORKLOADS[workload]
+    ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"]
+    grid = hdg_inputs.grid_lines(ne, cfg["stretched"])
+    h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
+    pr = Problem(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT, lam)
+    assert h.trace_size == pr.mesh.n_trace
+    x = hdg_inputs.uniform_pm1(h.trace_size, 11893)
+    y = h.apply(torch.tensor(x, device="cuda"), lam).cpu().numpy()
+    rng = np.random.default_rng(4)
+    dofs = np.concatenate([rng.choice(h.trace_size, 12, replace=False), [0, h.trace_size - 1]])
+    ref = pr.apply_rows(x, dofs)
+    assert np.abs(y[dofs] - ref).max() <= 1e-12 * np.abs(ref).max()
+    y32 = h.apply(torch.tensor(x, device="cuda", dtype=torch.float32), lam).double().cpu().numpy()
+    assert np.abs(y32[dofs] - ref).max() <= 1e-5 * np.abs(ref).max()

@@ -1,0 +1,156 @@
+"""GPU parity of the solve (hdg_solve), recovery and adjoint against the oracle.
+
+* Solves stop on ||F - K ut||_2 <= tol ||F||_2 in the nodal basis; the
+  oracle re-evaluates that residual with its own dense-condensed K and F.
+* The recovered u must equal the oracle's recovery of the GPU traces.
+* Polynomial data are reproduced through the GPU path with inhomogeneous
+  Dirichlet and Neumann data.
+* Adjoint gradients match the oracle's dense adjoint.
+"""
+import numpy as np
+import pytest
+import torch
+
+import hdg_inputs
+from oracle.solver import Problem
+from tests._poly import PolyField, boundary_data
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2007_11891_gb300 import build
+    build.build(verbose=False)
+
+
+def _stretched(ne, seed):
+    rng = np.random.default_rng(seed)
+    return [np.concatenate([[0.0], np.cumsum(rng.uniform(0.5, 2.0, ne[d]))]) for d in range(3)]
+
+
+def _oracle_residual(pr, trace, f=None, bdry=None, b=None):
+    K, _ = pr.assemble()
+    F = pr.rhs(f=f, bdry=bdry, b=b)
+    return np.linalg.norm(F - K @ trace) / np.linalg.norm(F)
+
+
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+def test_unit_cube_p4_manufactured(inner):
+    from paper_2007_11891_gb300 import HDG
+    cfg = hdg_inputs.WORKLOADS["unit_cube_p4"]
+    ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"]
+    grid = hdg_inputs.grid_lines(ne)
+    h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
+    pr = Problem(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT, lam)
+    f = hdg_inputs.sinsinsin_load(pr.mesh.volume_coords(pr.m1.nodes), lam)
+    tr, u, info = h.solve(torch.tensor(f, device="cuda"), lam, tol=1e-10, inner=inner)
+    tr, u = tr.cpu().numpy(), u.cpu().numpy()
+    assert info[0]["status"] == "OK" and info[0]["rel_residual"] <= 1e-10
+    assert _oracle_residual(pr, tr, f=f) <= 1e-10
+    u_ref, _ = pr.recover(tr, f=f)
+    assert np.abs(u - u_ref).max() <= 1e-10 * np.abs(u_ref).max()
+    # discretisation error against the exact solution (order p+1 regime)
+    u_ex = hdg_inputs.sinsinsin(pr.mesh.volume_coords(pr.m1.nodes))
+    assert np.abs(u - u_ex).max() < 1e-3
+
+
+@pytest.mark.parametrize("bc,p", [((0, 1, 0, 0, 1, 0), 3), ((1, 0, 0, 1, 0, 0), 2), ((0,) * 6, 5)])
+def test_polynomial_reproduction_inhomogeneous(bc, p):
+    from paper_2007_11891_gb300 import HDG
+    ne = (3, 2, 3)
+    grid = _stretched(ne, p)
+    lam = 0.8
+    pr = Problem(ne, grid, bc, p, 25.0, lam)
+    h = HDG(ne, grid, bc, p, 25.0)
+    fld = PolyField(p, np.random.default_rng(p))
+    X = pr.mesh.volume_coords(pr.m1.nodes)
+    f = lam * fld.u(X) - fld.lap(X)
+    bd = boundary_data(pr, fld)
+    tr, u, info = h.solve(torch.tensor(f, device="cuda"), lam, bdry=torch.tensor(bd, device="cuda"),
+                          tol=1e-13, inner="fp64")
+    tr, u = tr.cpu().numpy(), u.cpu().numpy()
+    scale = np.abs(fld.u(X)).max()
+    assert np.abs(u - fld.u(X)).max() <= 1e-9 * scale
+    assert np.abs(tr - fld.u(pr.mesh.trace_coords(pr.m1.nodes))).max() <= 1e-9 * scale
+    assert _oracle_residual(pr, tr, f=f, bdry=bd) <= 1e-12
+
+
+def test_stretched_mixed_precision_solve_and_recovery():
+    from paper_2007_11891_gb300 import HDG
+    ne, p, lam = (5, 4, 3), 4, 10.0
+    grid = _stretched(ne, 17)
+    bc = (0, 0, 1, 0, 0, 1)
+    h = HDG(ne, grid, bc, p, 25.0)
+    pr = Problem(ne, grid, bc, p, 25.0, lam)
+    f = hdg_inputs.gaussian(h.volume_size, 11890)
+    rng = np.random.default_rng(2)
+    bd = rng.standard_normal(h.boundary_size)
+    tr, u, info = h.solve(torch.tensor(f, device="cuda"), lam, bdry=torch.tensor(bd, device="cuda"),
+                          tol=1e-10, inner="fp32")
+    tr, u = tr.cpu().numpy(), u.cpu().numpy()
+    assert info[0]["outer"] >= 2       # FP32 inner solves need refinement
+    assert _oracle_residual(pr, tr, f=f, bdry=bd) <= 1e-10
+    u_ref, _ = pr.recover(tr, f=f, bdry=bd)
+    assert np.abs(u - u_ref).max() <= 1e-10 * np.abs(u_ref).max()
+
+
+def test_batched_solve_matches_single():
+    from paper_2007_11891_gb300 import HDG
+    ne, p = (4, 3, 4), 3
+    grid = hdg_inputs.grid_lines(ne)
+    lams = hdg_inputs.batch_lambdas(5)
+    h = HDG(ne, grid, (0,) * 6, p, 25.0)
+    F = np.stack([hdg_inputs.gaussian(h.volume_size, 100 + r) for r in range(len(lams))])
+    tr, u, info = h.solve(torch.tensor(F, device="cuda"), lams, tol=1e-10, inner="fp32")
+    tr = tr.cpu().numpy()
+    for r, lam in enumerate(lams):
+        pr = Problem(ne, grid, (0,) * 6, p, 25.0, lam)
+        assert _oracle_residual(pr, tr[r], f=F[r]) <= 1e-10
+        assert info[r]["status"] == "OK"
+        t1, _, _ = h.solve(torch.tensor(F[r], device="cuda"), float(lam), tol=1e-10, inner="fp32",
+                           return_u=False)
+        assert np.abs(t1.cpu().numpy() - tr[r]).max() <= 1e-8 * np.abs(tr[r]).max()
+
+
+def test_singular_is_reported():
+    from paper_2007_11891_gb300 import HDG, _capi
+    ne = (2, 2, 2)
+    h = HDG(ne, hdg_inputs.grid_lines(ne), (1,) * 6, 2, 25.0)
+    f = torch.ones(h.volume_size, dtype=torch.float64, device="cuda")
+    with pytest.raises(_capi.HdgError) as ei:
+        h.solve(f, 0.0)
+    assert ei.value.status == 2
+
+
+@pytest.mark.parametrize("ne,p", [((2, 2, 2), 2), ((4, 4, 4), 3)])
+def test_adjoint_matches_oracle(ne, p):
+    from paper_2007_11891_gb300 import HDG
+    lam = 5.0
+    grid = hdg_inputs.grid_lines(ne)
+    pr = Problem(ne, grid, (0,) * 6, p, 25.0, lam)
+    h = HDG(ne, grid, (0,) * 6, p, 25.0)
+    X = pr.mesh.volume_coords(pr.m1.nodes)
+    f = hdg_inputs.gaussian(len(X), 11897)
+    ut = hdg_inputs.smooth_target(X, hdg_inputs.smooth_target_coeffs())
+    L, dLdf, dLdlam, u_ref = pr.adjoint(f, ut, method="direct")
+    _, u, _ = h.solve(torch.tensor(f, device="cuda"), lam, tol=1e-13, inner="fp64")
+    assert np.abs(u.cpu().numpy() - u_ref).max() <= 1e-9 * np.abs(u_ref).max()
+    gf, gl, info = h.solve_adjoint(u, 2.0 * (u - torch.tensor(ut, device="cuda")), lam, tol=1e-13, inner="fp64")
+    assert np.abs(gf.cpu().numpy() - dLdf).max() <= 1e-8 * np.abs(dLdf).max()
+    assert abs(float(gl[0]) - dLdlam) <= 1e-8 * abs(dLdlam)
+
+
+def test_autograd_function():
+    from paper_2007_11891_gb300 import HDG, HDGSolve
+    ne, p = (3, 3, 3), 2
+    grid = hdg_inputs.grid_lines(ne)
+    h = HDG(ne, grid, (0,) * 6, p, 25.0)
+    f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 1), device="cuda", requires_grad=True)
+    lam = torch.tensor([2.0], dtype=torch.float64, device="cuda", requires_grad=True)
+    u = HDGSolve.apply(f, lam, h, 1e-12, "fp64")
+    loss = (u ** 2).sum()
+    loss.backward()
+    gf, gl, _ = h.solve_adjoint(u.detach(), 2.0 * u.detach(), [2.0], tol=1e-12, inner="fp64")
+    assert torch.allclose(f.grad, gf, rtol=1e-9, atol=1e-12 * float(gf.abs().max()))
+    assert torch.allclose(lam.grad, gl, rtol=1e-9)
