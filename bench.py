@@ -1,0 +1,353 @@
+"""Benchmark: condensed-operator throughput and CG solve time to 1e-10, mixed vs FP64.
+
+Workload (one step): one full solve of the 16^3 stretched-grid Helmholtz
+problem (p = 8, lambda = 10, f ~ N(0, 1) per volume node) through hdg_solve
+with device-resident inputs: transformed right-hand side, FP32 transformed CG
+inside FP64 iterative refinement to ||F - K ut|| <= 1e-10 ||F|| (nodal
+basis), traces back-transformed, u recovered.  L2 is flushed (a 256 MB
+write) before every timed step.
+
+value = trace DOFs x condensed-operator applications per step / step time
+(GDOF/s), summed over ranks.  Each rank solves its own replica (different
+seed): the mesh is not partitioned across GPUs ("scaling": "weak").
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import hdg_inputs  # noqa: E402
+
+METRIC = "condensed-operator GDOF/s + CG solve time to 1e-10, mixed vs FP64 on 1 GB300"
+WORKLOAD = "stretched_p8"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2 flops x 2070 MHz (recipe's unit
+# counts and maximum clock); measured 1.19 TFLOP/s at 1987 MHz with an FMA loop
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU reference (the oracle), bounded sample of the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(m):
+    """Oracle solve on the m x m x m corner of the stretched 16^3 grid (same
+    p, lambda, tau_hat, load distribution).  Returns (trace DOFs, operator
+    applications, seconds)."""
+    from oracle.solver import Problem
+    cfg = hdg_inputs.WORKLOADS[WORKLOAD]
+    grid = hdg_inputs.grid_lines(cfg["ne"], cfg["stretched"])
+    sub = [g[:m + 1] for g in grid]
+    t0 = time.perf_counter()
+    pr = Problem((m, m, m), sub, (0,) * 6, cfg["p"], hdg_inputs.TAU_HAT, cfg["lam"])
+    f = hdg_inputs.gaussian(pr.mesh.n_elem * (cfg["p"] + 1) ** 3, 11890)
+    _, _, _, info = pr.solve(f=f, tol=1e-10)
+    dt = time.perf_counter() - t0
+    return pr.mesh.n_trace, info["iters"] + 1, dt
+
+
+def cpu_baseline(m=3):
+    T, applies, dt = oracle_sample(m)
+    return {"value": T * applies / dt / 1e9, "unit": "GDOF/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle solve (dense LU/Cholesky condensation per element, plain CG to 1e-10) on the "
+                      "%dx%dx%d corner of the stretched 16^3 grid, p=8, lambda=10: %d trace DOFs, %d operator "
+                      "applications, %.1f s; numpy/scipy BLAS threads up to cores" % (m, m, m, T, applies, dt)}
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    m = 2
+    for _ in range(args.warmup):
+        oracle_sample(m)
+    tot, work = 0.0, 0.0
+    for _ in range(args.steps):
+        T, applies, dt = oracle_sample(m)
+        tot += dt
+        work += T * applies
+    value = work / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "%s: oracle solve on the 2x2x2 corner of the 16^3 stretched grid, p=8, "
+                                   "lambda=10, f~N(0,1), CG to 1e-10" % WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": "2x2x2 corner of the stretched 16^3 grid per step"},
+            "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2007_11891_gb300 import HDG
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    cfg = hdg_inputs.WORKLOADS[WORKLOAD]
+    ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"]
+    grid = hdg_inputs.grid_lines(ne, cfg["stretched"])
+    h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
+    T, V = h.trace_size, h.volume_size
+    f = torch.tensor(hdg_inputs.gaussian(V, 11890 + rank), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def timed(fn, steps):
+        """Per-step CUDA-event time (ms) with an L2 flush before each step."""
+        evs = []
+        infos = None
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            infos = fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs), infos
+
+    solve_mixed = lambda: h.solve(f, lam, tol=1e-10, inner="fp32")[2]
+    solve_fp64 = lambda: h.solve(f, lam, tol=1e-10, inner="fp64")[2]
+
+    for _ in range(args.warmup):
+        solve_mixed()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    ms, infos = timed(solve_mixed, args.steps)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    clocks = clk.stop()
+    applies = infos[0]["applies"]
+    ms_step = ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t[0])
+    value = world * T * applies / (ms_step * 1e-3) / 1e9
+
+    # FP64 solve with the same machinery (FP64 inner CG)
+    solve_fp64()
+    n64 = max(2, args.steps // 5)
+    ms64, infos64 = timed(solve_fp64, n64)
+    ms64 /= n64
+
+    # end to end through the public API with host buffers
+    f_host = torch.empty(V, dtype=torch.float64, pin_memory=True)
+    f_host.copy_(f.cpu())
+    u_host = torch.empty(V, dtype=torch.float64, pin_memory=True)
+    t_host = torch.empty(T, dtype=torch.float64, pin_memory=True)
+
+    def e2e_step():
+        fd = f_host.to(dev, non_blocking=True)
+        tr, u, inf = h.solve(fd, lam, tol=1e-10, inner="fp32")
+        u_host.copy_(u, non_blocking=True)
+        t_host.copy_(tr, non_blocking=True)
+        return inf
+
+    e2e_step()
+    ms_e2e, _ = timed(e2e_step, args.steps)
+    ms_e2e /= args.steps
+
+    # isolated operator applications (transformed basis), L2 flushed per launch
+    x64 = torch.tensor(hdg_inputs.uniform_pm1(T, 11893), device=dev)
+    x32 = x64.float()
+    app = {}
+    for name, x in (("fp64", x64), ("fp32", x32)):
+        y = torch.empty_like(x)
+        for _ in range(3):
+            h.apply(x, lam, basis="transformed", out=y)
+        ms_a, _ = timed(lambda: h.apply(x, lam, basis="transformed", out=y), 20)
+        app[name] = {"us": 1e3 * ms_a / 20, "gdofs": T / (ms_a / 20 * 1e-3) / 1e9}
+
+    # live kernel timing inside one profiled mixed solve (events on the launch stream)
+    h.profile(True)
+    flush.fill_(1.0)
+    _, _, pinfo = h.solve(f, lam, tol=1e-10, inner="fp32")
+    classes = {}
+    for k in h.KERNEL_CLASSES:
+        tot_ms, cnt = h.profile_read(k)
+        if cnt:
+            classes[k] = {"ms": tot_ms, "launches": cnt}
+    _, launches_per_solve = h.profile_read("all")
+    h.profile(False)
+    dominant = max(classes, key=lambda k: classes[k]["ms"])
+    pk, src = peaks()
+    n = p + 1
+    ne_tot = ne[0] * ne[1] * ne[2]
+
+    def roof(kind):
+        c = classes[kind]
+        avg_s = c["ms"] / c["launches"] * 1e-3
+        if kind == "op_fp32":
+            byts = 2.0 * T * 4
+            ach = byts / avg_s / 1e9
+            return {"kernel": "tpt_kernel<float> (operator, FP32)", "bound": "hbm", "achieved": ach,
+                    "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+                    "peak_source": "of " + src, "avg_launch_us": avg_s * 1e6,
+                    "algorithmic_bytes_per_launch": byts}
+        if kind == "op_fp64":
+            flops = (12.0 * n ** 3 + 24.0 * n ** 2) * ne_tot
+            ach = flops / avg_s / 1e12
+            return {"kernel": "tpt_kernel<double> (operator, FP64)", "bound": "alu", "achieved": ach,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs at 2070 MHz", "avg_launch_us": avg_s * 1e6,
+                    "algorithmic_flops_per_launch": flops}
+        if kind in ("face", "volume", "rhs_recover"):
+            if kind == "face":
+                flops = 4.0 * n ** 3 * (T // (n * n))
+            elif kind == "volume":
+                flops = 6.0 * n ** 4 * ne_tot
+            else:
+                flops = (12.0 * n ** 3 + 24.0 * n ** 2) * ne_tot
+            ach = flops / avg_s / 1e12
+            return {"kernel": kind + " (FP64)", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs at 2070 MHz", "avg_launch_us": avg_s * 1e6,
+                    "algorithmic_flops_per_launch": flops}
+        byts = 7.0 * T * 4
+        ach = byts / avg_s / 1e9
+        return {"kernel": "CG vector kernels", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": "of " + src,
+                "avg_launch_us": avg_s * 1e6}
+
+    roofline = roof(dominant)
+    roofline["share_of_solve"] = classes[dominant]["ms"] / sum(c["ms"] for c in classes.values())
+    others = {k: roof(k) for k in classes if k != dominant}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "%s: 16x16x16 stretched grid (widths U[0.5,2], seeded), p=8, lambda=10, "
+                               "tau_hat=25, Dirichlet, f~N(0,1); one full mixed-precision solve per step "
+                               "(FP32 transformed CG inside FP64 refinement) to 1e-10" % WORKLOAD,
+                   "trace_dofs": T, "volume_dofs": V, "l2": "flushed before each step (256 MB write)",
+                   "parallelism": "replicas (one independent solve per GPU)"},
+        "clocks": clocks,
+        "e2e": {"value": world * T * applies / (ms_e2e * 1e-3) / 1e9, "unit": "GDOF/s",
+                "h2d_bytes_per_step": V * 8, "d2h_bytes_per_step": (V + T) * 8, "ms_per_step": ms_e2e},
+        "gpu_launches": launches_per_solve * args.steps,
+        "roofline": roofline,
+        "roofline_other_kernels": others,
+        "solve": {"mixed_ms": ms_step, "fp64_ms": ms64, "speedup_mixed_vs_fp64": ms64 / ms_step,
+                  "mixed": infos[0], "fp64": infos64[0], "wall_s_timed": wall},
+        "apply_isolated_transformed": app,
+        "kernel_time_by_class_ms": classes,
+    }
+    if rank == 0:
+        if world == 1:
+            try:
+                line["cpu_baseline"] = cpu_baseline()
+            except Exception as exc:  # the oracle is optional on the GPU machine
+                line["cpu_baseline"] = {"value": None, "unit": "GDOF/s", "kind": "oracle", "error": str(exc)}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
