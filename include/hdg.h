@@ -146,6 +146,38 @@ hdg_status hdg_get_nodes(const hdg_ctx* ctx, double* h_nodes);
 hdg_status hdg_apply(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_precision prec,
                      hdg_basis basis, const void* d_x, void* d_y, void* stream);
 
+/* The same product as hdg_apply(ctx, nrhs, h_lambda, HDG_FP64,
+ * HDG_BASIS_NODAL, d_x, d_y, stream), for callers that must not allocate
+ * device memory.  The paper has no counterpart: this is an interface for
+ * such callers, not part of the method.
+ *
+ * Who needs it: code that runs while the program is capturing a CUDA graph
+ * (cudaMalloc and cudaFree are not allowed during capture, and cudaFree
+ * synchronises the whole device), real-time loops that must neither
+ * synchronise nor risk an allocation failure once running, and programs
+ * whose device memory is owned by a pooling allocator that forbids
+ * allocations made behind its back.  hdg_apply grows internal workspaces
+ * with cudaMalloc the first time a size or lambda is seen; this entry point
+ * never calls cudaMalloc, cudaFree or any allocating routine.
+ *
+ * Its temporaries (the face-eigenbasis traces before and after the
+ * operator, 2 x nrhs x hdg_trace_size() doubles, and the D_Z^-1 tables of
+ * the lambdas, nrhs x n^3 doubles on a uniform grid or nrhs x n_e x n^3 on a
+ * stretched one) live in one static device array of 2^21 doubles (16 MiB),
+ * which every GPU that loads the library reserves until the process exits.
+ * Larger requests are rejected with HDG_ERR_INVALID_ARG and a message
+ * giving the size needed (use hdg_apply then).
+ *
+ * The first call on a device looks up that array's device address with
+ * that device current; make that first call before any stream capture.
+ * All calls share the one array, which keeps the previous call's contents:
+ * calls whose work overlaps on the GPU (different streams, or different
+ * host threads) race on it and must be serialised by the caller.
+ * Arguments, layout and results are those of hdg_apply with FP64 nodal
+ * traces; the current device must be the context's device.              */
+hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_lambda, const double* d_x, double* d_y,
+                            void* stream);
+
 /* Solve K ut = F (Alg. (hdg_cg) with the transformed CG of
  * Alg. (hdg_transformed_cg)) for nrhs right-hand sides, in FP64 or with an
  * FP32/BF16 inner CG inside FP64 iterative refinement.

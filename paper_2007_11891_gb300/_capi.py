@@ -15,7 +15,7 @@ PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 BASIS = {"nodal": 0, "transformed": 1}
 
 EXPORTED = ["hdg_setup", "hdg_destroy", "hdg_trace_size", "hdg_volume_size", "hdg_boundary_size",
-            "hdg_get_nodes", "hdg_apply", "hdg_solve", "hdg_solve_adjoint", "hdg_last_error",
+            "hdg_get_nodes", "hdg_apply", "hdg_apply_static", "hdg_solve", "hdg_solve_adjoint", "hdg_last_error",
             "hdg_status_string", "hdg_profile", "hdg_profile_read"]
 
 
@@ -72,6 +72,8 @@ def lib():
     L.hdg_get_nodes.restype = ci
     L.hdg_apply.argtypes = [vp, ci, pd, ci, ci, vp, vp, vp]
     L.hdg_apply.restype = ci
+    L.hdg_apply_static.argtypes = [vp, ci, pd, vp, vp, vp]
+    L.hdg_apply_static.restype = ci
     L.hdg_solve.argtypes = [vp, ci, pd, vp, vp, vp, vp, vp, ctypes.POINTER(HdgSolveOpts),
                             ctypes.POINTER(HdgSolveInfo), vp]
     L.hdg_solve.restype = ci

@@ -448,6 +448,26 @@ __global__ void negate_kernel(double* x, int n) {
 
 }  // namespace
 
+namespace hdg {
+bool ctx_view(const hdg_ctx* c, CtxView* v) {
+  if (!c || !v) return false;
+  v->device = c->device;
+  v->n = c->n;
+  v->uniform = c->uniform;
+  v->mesh = c->mesh;
+  v->tab = c->tab64;
+  v->metric64 = c->d_metric64;
+  v->Lambda = c->d_Lambda;
+  v->StM = c->StM;
+  v->MS = c->MS;
+  v->nelem = c->nelem;
+  v->ntrace = c->ntrace;
+  v->nclass = nclass(c);
+  return true;
+}
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace hdg
+
 extern "C" {
 
 const char* hdg_last_error(void) { return g_last_error.c_str(); }

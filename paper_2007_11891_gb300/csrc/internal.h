@@ -81,4 +81,23 @@ template <typename T>
 cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, long long len, int nrhs,
                               cudaStream_t s);
 
+// ---- read-only view of a context's device tables (hdg_api.cu) ----------------
+struct CtxView {
+  int device = 0;
+  int n = 0;
+  int uniform = 1;
+  MeshDev mesh{};
+  Tables<double> tab{};
+  const double* metric64 = nullptr;
+  const double* Lambda = nullptr;
+  Mat1D<double> StM{}, MS{};
+  long long nelem = 0, ntrace = 0, nclass = 0;
+};
+
+}  // namespace hdg
+
+struct hdg_ctx;
+namespace hdg {
+bool ctx_view(const hdg_ctx* c, CtxView* out);
+void set_last_error(const char* msg);
 }  // namespace hdg
