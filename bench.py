@@ -325,13 +325,119 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# extra measurements (not the contract line): operator sweep and batched solve
+# ---------------------------------------------------------------------------
+def run_sweep(args):
+    """One JSON line per measurement: the 32^3 operator sweep (p in
+    {2, 4, 8, 12, 16}, FP64 and FP32, transformed basis, L2 flushed per
+    launch) against its roofline, and the 64-rhs batched solve (24^3, p = 7,
+    lambda from {0.1, 1, 100}) mixed vs FP64."""
+    import torch
+    from paper_2007_11891_gb300 import HDG
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    pk, src = peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def per_launch_ms(fn, reps):
+        tot = 0.0
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / reps
+
+    cfg = hdg_inputs.WORKLOADS["uniform32"]
+    ne = cfg["ne"]
+    grid = hdg_inputs.grid_lines(ne)
+    for p in (2, 4, 8, 12, 16):
+        h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
+        T = h.trace_size
+        n = p + 1
+        x64 = torch.tensor(hdg_inputs.uniform_pm1(T, 11893), device=dev)
+        for prec, x in (("fp64", x64), ("fp32", x64.float())):
+            y = torch.empty_like(x)
+            h.apply(x, cfg["lam"], basis="transformed", out=y)
+            ms = per_launch_ms(lambda: h.apply(x, cfg["lam"], basis="transformed", out=y), 10)
+            line = {"sweep": "operator", "workload": "uniform32", "p": p, "precision": prec,
+                    "trace_dofs": T, "us_per_apply": ms * 1e3, "gdofs": T / (ms * 1e-3) / 1e9}
+            if prec == "fp32":
+                ach = 2.0 * T * 4 / (ms * 1e-3) / 1e9
+                line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                    "frac": ach / pk["hbm_gbs"], "peak_source": "of " + src}
+            else:
+                flops = (12.0 * n ** 3 + 24.0 * n ** 2) * ne[0] * ne[1] * ne[2]
+                ach = flops / (ms * 1e-3) / 1e12
+                line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                    "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "derived FP64 pipe"}
+            print(json.dumps(line), flush=True)
+        h.close()
+        del x64
+    # batched solve
+    cfg = hdg_inputs.WORKLOADS["batched24_p7"]
+    ne, p, nrhs = cfg["ne"], cfg["p"], cfg["nrhs"]
+    h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, p, hdg_inputs.TAU_HAT)
+    lams = hdg_inputs.batch_lambdas(nrhs)
+    F = torch.tensor(np.stack([hdg_inputs.gaussian(h.volume_size, 11894 + r) for r in range(nrhs)]), device=dev)
+    for inner in ("fp32", "fp64"):
+        h.solve(F, lams, tol=1e-10, inner=inner)
+        ms = per_launch_ms(lambda: h.solve(F, lams, tol=1e-10, inner=inner), 2)
+        _, _, info = h.solve(F, lams, tol=1e-10, inner=inner)
+        print(json.dumps({"sweep": "batched_solve", "workload": "batched24_p7", "nrhs": nrhs, "inner": inner,
+                          "ms": ms, "trace_dofs_per_rhs": h.trace_size,
+                          "max_iterations": max(i["iterations"] for i in info),
+                          "max_rel_residual": max(i["rel_residual"] for i in info),
+                          "all_ok": all(i["status"] == "OK" for i in info)}), flush=True)
+
+
+def run_probe(args):
+    """Short, untimed workload for ncu captures: set-up, one warm-up, then
+    `--steps` repetitions of the probed step (mixed solve, or one operator
+    application in FP32/FP64 in the transformed basis) on the bench workload."""
+    import torch
+    from paper_2007_11891_gb300 import HDG
+    torch.cuda.set_device(0)
+    cfg = hdg_inputs.WORKLOADS[args.workload]
+    ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"] or 1.0
+    h = HDG(ne, hdg_inputs.grid_lines(ne, cfg["stretched"]), (0,) * 6, p, hdg_inputs.TAU_HAT)
+    if args.probe == "solve":
+        f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11890), device="cuda")
+        step = lambda: h.solve(f, lam, tol=1e-10, inner="fp32", return_u=True)
+    else:
+        dt = torch.float32 if args.probe == "apply32" else torch.float64
+        x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device="cuda", dtype=dt)
+        y = torch.empty_like(x)
+        step = lambda: h.apply(x, lam, basis="transformed", out=y)
+    step()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    print("probe done", args.probe, args.workload, h.trace_size)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweep", action="store_true", help="extra measurements instead of the bench line")
+    ap.add_argument("--probe", choices=["solve", "apply32", "apply64"], help="untimed workload for ncu")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(hdg_inputs.WORKLOADS))
     args = ap.parse_args()
+    if args.probe:
+        run_probe(args)
+        return
+    if args.sweep:
+        run_sweep(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

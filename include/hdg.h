@@ -105,6 +105,9 @@ typedef struct {
   hdg_precision inner;     /* precision of the inner CG (FP64, FP32 or BF16)      */
   double inner_tol;        /* relative residual reduction per inner solve;
                               <= 0 picks 1e-5 for FP32/BF16 and tol for FP64      */
+  int precond;             /* 0: plain CG; 1: face-block Jacobi preconditioner of
+                              Sec. 5.1 (Alg. hdg_pc_block), diagonal in the
+                              transformed basis (the paper's HDG-trans solver)     */
 } hdg_solve_opts;
 
 typedef struct {
@@ -204,6 +207,14 @@ hdg_status hdg_solve(hdg_ctx* ctx, int nrhs, const double* h_lambda, const doubl
 hdg_status hdg_solve_adjoint(hdg_ctx* ctx, int nrhs, const double* h_lambda, const double* d_u,
                              const double* d_grad_u, double* d_grad_f, double* d_grad_lambda,
                              const hdg_solve_opts* opts, hdg_solve_info* h_info, void* stream);
+
+/* Tuning (not part of the method): the length, in elements, of the x1-pencil
+ * segments that one CTA slot of the operator kernel marches over (faces
+ * inside a segment are summed in registers, faces on segment ends with two
+ * atomic adds).  0 restores the automatic choice (enough segments to fill
+ * the GPU).  Speed only: every value gives bitwise identical results.
+ * Errors: INVALID_ARG (NULL context, negative length).                    */
+hdg_status hdg_set_x1_segment(hdg_ctx* ctx, int elements);
 
 /* Measurement support (not part of the method).  Kernel classes:
  *   0 condensed operator, FP32 arithmetic   1 condensed operator, FP64

@@ -70,6 +70,19 @@ struct hdg_ctx {
   long long launches = 0;
   std::vector<cudaEvent_t> ev[6];
   size_t ev_used[6] = {0, 0, 0, 0, 0, 0};
+  // preconditioner for the lambdas of the last call
+  std::vector<double> pc_lam;
+  DevBuf pc_diag, pc_w64, pc_w32;
+  // CUDA graphs of the inner CG loop
+  struct GraphEntry {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec;
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t cap_stream = nullptr;
+  bool capturing = false;
+  int graphs_enabled = 1;
+  int seg_override = 0;   // x1 segment length; 0 = automatic
 };
 
 namespace {
@@ -97,6 +110,8 @@ hdg_status ensure(DevBuf& b, size_t bytes) {
 template <typename T>
 T* wsp(hdg_ctx* c, int i) { return static_cast<T*>(c->ws[i].p); }
 
+using GraphEntry = hdg_ctx::GraphEntry;
+
 enum KernelClass { K_OP32 = 0, K_OP64 = 1, K_FACE = 2, K_VOL = 3, K_RHS = 4, K_VEC = 5 };
 
 // Counts a launch and, while profiling, brackets it with an event pair.
@@ -106,6 +121,7 @@ struct Timed {
   cudaStream_t s;
   long long idx = -1;
   Timed(hdg_ctx* c_, int cls_, cudaStream_t s_) : c(c_), cls(cls_), s(s_) {
+    if (c->capturing) return;   // counted when the graph is launched
     c->launches += 1;
     if (!c->prof_on) return;
     std::vector<cudaEvent_t>& v = c->ev[cls];
@@ -161,7 +177,7 @@ hdg_status ensure_dinv(hdg_ctx* c, int nrhs, const double* lam, cudaStream_t s, 
 }
 
 template <typename T, typename ST>
-hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv) {
+hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs) {
   hdg::TptArgs<T, ST> a{};
   a.mesh = c->mesh;
   a.tab = tables<T>(c);
@@ -173,24 +189,31 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv) {
   a.vol_stride = c->nvol;
   a.ppb = hdg::tpt_ppb(c->n);
   a.npencils = (long long)c->mesh.ne[1] * c->mesh.ne[2];
+  hdg::tpt_split(c->n, c->mesh.ne, nrhs, &a.seg, &a.nseg);
+  if (c->seg_override > 0) {
+    a.seg = std::min(c->seg_override, c->mesh.ne[0]);
+    a.nseg = (c->mesh.ne[0] + a.seg - 1) / a.seg;
+  }
   return a;
 }
 
-// zero the x2/x3 blocks of nrhs trace vectors (x1 faces are stored, not added)
+// Zero what the operator accumulates with atomics: the x2/x3 blocks, and the
+// whole vector when x1-pencils are split into several segments.
 template <typename ST>
-hdg_status zero_x23(const hdg_ctx* c, ST* y, int nrhs, cudaStream_t s) {
-  const long long off = c->mesh.blk[1] * (long long)c->n * c->n;
+hdg_status zero_for_tpt(const hdg_ctx* c, ST* y, int nrhs, int nseg, cudaStream_t s) {
+  const long long off = nseg > 1 ? 0 : c->mesh.blk[1] * (long long)c->n * c->n;
   const long long cnt = c->ntrace - off;
   if (cnt <= 0) return HDG_OK;
   HDG_CUDA(cudaMemset2DAsync(y + off, sizeof(ST) * c->ntrace, 0, sizeof(ST) * cnt, nrhs, s));
   return HDG_OK;
 }
 
+// y = K-hat x; `zeroed` says the caller already zeroed y (the CG update does)
 template <typename T, typename ST>
 hdg_status tpt_apply(hdg_ctx* c, int nrhs, const T* dinv, const ST* x, ST* y, cudaStream_t s,
-                     const int* skip = nullptr, hdg::CgHook hook = hdg::CgHook{}) {
-  HDG_TRY(zero_x23<ST>(c, y, nrhs, s));
-  hdg::TptArgs<T, ST> a = base_args<T, ST>(c, dinv);
+                     const int* skip = nullptr, hdg::CgHook hook = hdg::CgHook{}, bool zeroed = false) {
+  hdg::TptArgs<T, ST> a = base_args<T, ST>(c, dinv, nrhs);
+  if (!zeroed) HDG_TRY(zero_for_tpt<ST>(c, y, nrhs, a.nseg, s));
   a.x = x;
   a.y = y;
   a.skip = skip;
@@ -214,8 +237,9 @@ int reduction_blocks(long long len) {
 }
 
 hdg_status ensure_reductions(hdg_ctx* c, int nrhs) {
-  c->red_blocks = 152 * 8;   // upper bound on blocks of any reducing launch
-  const long long tpt_b = hdg::tpt_blocks((long long)c->mesh.ne[1] * c->mesh.ne[2], hdg::tpt_ppb(c->n));
+  c->red_blocks = 152 * 8;   // upper bound on blocks of any reducing vector launch
+  // the operator grid is largest when every pencil is split into single elements
+  const long long tpt_b = hdg::tpt_blocks(c->nelem, hdg::tpt_ppb(c->n));
   const long long pb = std::max<long long>(c->red_blocks, tpt_b);
   HDG_TRY(ensure(c->partials, sizeof(double) * (size_t)nrhs * pb));
   const bool fresh = c->counters.bytes < sizeof(unsigned int) * (size_t)nrhs;
@@ -228,18 +252,121 @@ hdg_status ensure_reductions(hdg_ctx* c, int nrhs) {
 }
 
 template <typename T>
-hdg_status dot(hdg_ctx* c, const T* a, const T* b, long long len, int nrhs, double* out, cudaStream_t s) {
+hdg_status dot(hdg_ctx* c, const T* a, const T* b, long long len, int nrhs, double* out, cudaStream_t s,
+               const T* w = nullptr) {
   Timed t(c, K_VEC, s);
-  HDG_CUDA(hdg::launch_dot<T>(a, b, len, nrhs, static_cast<double*>(c->partials.p),
+  HDG_CUDA(hdg::launch_dot<T>(a, b, w, len, nrhs, static_cast<double*>(c->partials.p),
                               static_cast<unsigned int*>(c->counters.p), out, reduction_blocks(len), s));
   return HDG_OK;
 }
 
-// Inner CG on K-hat d = rhat in precision T for the right-hand sides with
-// active[r] != 0; returns per-rhs iterations and status.
+// Face-block Jacobi preconditioner (Sec. 5.1) for the lambdas of the call:
+// inverse face self-coupling of K-hat, FP64 and FP32 copies.
+hdg_status ensure_pc(hdg_ctx* c, int nrhs, const double* lam, cudaStream_t s) {
+  std::vector<double> want(lam, lam + nrhs);
+  if (c->pc_lam == want) return HDG_OK;
+  const double* dinv = nullptr;
+  HDG_TRY(ensure_dinv<double>(c, nrhs, lam, s, &dinv));
+  const size_t tot = (size_t)c->ntrace * nrhs;
+  HDG_TRY(ensure(c->pc_diag, sizeof(double) * tot));
+  HDG_TRY(ensure(c->pc_w64, sizeof(double) * tot));
+  HDG_TRY(ensure(c->pc_w32, sizeof(float) * tot));
+  HDG_CUDA(cudaMemsetAsync(c->pc_diag.p, 0, sizeof(double) * tot, s));
+  { Timed t_(c, K_VEC, s);
+    HDG_CUDA(hdg::launch_pc_diag(c->mesh, c->n, c->tab64, c->d_metric64, dinv, nclass(c) * n3(c),
+                                 static_cast<double*>(c->pc_diag.p), nrhs, c->ntrace, s)); }
+  { Timed t_(c, K_VEC, s);
+    HDG_CUDA(hdg::launch_pc_invert(static_cast<double*>(c->pc_diag.p), static_cast<double*>(c->pc_w64.p),
+                                   static_cast<float*>(c->pc_w32.p), (long long)tot, s)); }
+  c->pc_lam = want;
+  return HDG_OK;
+}
+
+template <typename T>
+const T* pc_weights(const hdg_ctx* c);
+template <>
+const double* pc_weights<double>(const hdg_ctx* c) { return static_cast<const double*>(c->pc_w64.p); }
+template <>
+const float* pc_weights<float>(const hdg_ctx* c) { return static_cast<const float*>(c->pc_w32.p); }
+
+// `count` CG iterations: operator (fused p^T q), update (alpha, d, r, q = 0,
+// r^T W r, beta), search-direction update.  Three kernels per iteration.
+template <typename T>
+hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, int count,
+                         cudaStream_t s) {
+  const long long T_ = c->ntrace;
+  int* flags = static_cast<int*>(c->flags.p);
+  hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
+  double* pq = static_cast<double*>(c->scal.p) + nrhs;
+  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), pq};
+  const int vb = reduction_blocks(T_);
+  for (int k = 0; k < count; ++k) {
+    HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, p, q, s, flags, hook, true)));
+    { Timed t_(c, K_VEC, s);
+      HDG_CUDA(hdg::launch_cg_update<T>(cg, flags, pq, d, r, p, q, w, T_, nrhs, static_cast<double*>(c->partials.p),
+                                        static_cast<unsigned int*>(c->counters.p), vb, s)); }
+    { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, w, T_, nrhs, s)); }
+  }
+  return HDG_OK;
+}
+
+// Replays `count` iterations from a CUDA graph captured once per
+// configuration (pointers, nrhs, precision); returns false (and leaves
+// graphs off) if capture is not possible, so the caller runs eagerly.
+template <typename T>
+bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, int count,
+              cudaStream_t s, hdg_status* st) {
+  *st = HDG_OK;
+  if (!c->graphs_enabled || c->prof_on) return false;
+  std::vector<uintptr_t> key = {sizeof(T), (uintptr_t)nrhs, (uintptr_t)dinv, (uintptr_t)w, (uintptr_t)r,
+                                (uintptr_t)d, (uintptr_t)p, (uintptr_t)q, (uintptr_t)c->flags.p,
+                                (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p, (uintptr_t)c->partials.p,
+                                (uintptr_t)c->counters.p, (uintptr_t)count};
+  GraphEntry* ge = nullptr;
+  for (GraphEntry& g : c->graphs)
+    if (g.key == key) ge = &g;
+  if (!ge) {
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      c->graphs_enabled = 0;
+      return false;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      c->graphs_enabled = 0;
+      cudaGetLastError();
+      return false;
+    }
+    c->capturing = true;
+    hdg_status cs = cg_iterations<T>(c, nrhs, dinv, w, r, d, p, q, count, c->cap_stream);
+    c->capturing = false;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (cs != HDG_OK || e != cudaSuccess || graph == nullptr ||
+        cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      c->graphs_enabled = 0;
+      cudaGetLastError();
+      g_last_error.clear();
+      return false;
+    }
+    cudaGraphDestroy(graph);
+    c->graphs.push_back(GraphEntry{key, exec});
+    ge = &c->graphs.back();
+  }
+  cudaError_t e = cudaGraphLaunch(ge->exec, s);
+  if (e != cudaSuccess) {
+    *st = fail(HDG_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+    return true;
+  }
+  c->launches += 3LL * count;
+  return true;
+}
+
+// Inner (preconditioned) CG on K-hat d = rhat in precision T for the
+// right-hand sides with active[r] != 0; returns per-rhs iterations and status.
 template <typename T>
 hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat, double tol_inner,
-                    const std::vector<int>& active, const std::vector<int>& max_it,
+                    const std::vector<int>& active, const std::vector<int>& max_it, bool use_pc,
                     std::vector<int>& iters, std::vector<int>& status, cudaStream_t s) {
   const long long T_ = c->ntrace;
   const long long tot = T_ * nrhs;
@@ -250,16 +377,21 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   T* q = wsp<T>(c, W_Q);
   const T* dinv = nullptr;
   HDG_TRY(ensure_dinv<T>(c, nrhs, lam, s, &dinv));
-  double* rr0 = static_cast<double*>(c->scal.p);
-  double* pq = rr0 + nrhs;
+  const T* w = nullptr;
+  if (use_pc) {
+    HDG_TRY(ensure_pc(c, nrhs, lam, s));
+    w = pc_weights<T>(c);
+  }
+  double* rz0 = static_cast<double*>(c->scal.p);
   int* flags = static_cast<int*>(c->flags.p);
   hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
 
   if (sizeof(T) == 8) HDG_CUDA(cudaMemcpyAsync(r, rhat, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
   else { Timed t_(c, K_VEC, s); HDG_CUDA((hdg::launch_convert<double, float>(rhat, reinterpret_cast<float*>(r), tot, s))); }
   HDG_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * tot, s));
-  HDG_CUDA(cudaMemcpyAsync(p, r, sizeof(T) * tot, cudaMemcpyDeviceToDevice, s));
-  HDG_TRY(dot<T>(c, r, r, T_, nrhs, rr0, s));
+  HDG_CUDA(cudaMemsetAsync(p, 0, sizeof(T) * tot, s));
+  HDG_CUDA(cudaMemsetAsync(q, 0, sizeof(T) * tot, s));
+  HDG_TRY(dot<T>(c, r, r, T_, nrhs, rz0, s, w));
   std::vector<int> hflags(nrhs);
   int maxit = 0;
   for (int i = 0; i < nrhs; ++i) {
@@ -268,18 +400,19 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   }
   HDG_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
   // the per-rhs cap is the largest; per-rhs caps below it are enforced on the host afterwards
-  { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_init(cg, flags, rr0, tol_inner, maxit, nrhs, s)); }
-  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), pq};
-  const int vb = reduction_blocks(T_);
+  { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_init(cg, flags, rz0, tol_inner, maxit, nrhs, s)); }
+  // p = W r (beta = 0 after init, p = 0)
+  { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, w, T_, nrhs, s)); }
   const int chunk = 16;
   std::vector<hdg::CgScalars> hcg(nrhs);
+  bool first = true;
   for (int done_it = 0; done_it < maxit; done_it += chunk) {
-    for (int k = 0; k < chunk; ++k) {
-      HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, p, q, s, flags, hook)));
-      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_update<T>(cg, flags, pq, d, r, p, q, T_, nrhs, static_cast<double*>(c->partials.p),
-                                        static_cast<unsigned int*>(c->counters.p), vb, s)); }
-      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, T_, nrhs, s)); }
-    }
+    hdg_status gs = HDG_OK;
+    // the first chunk runs eagerly (sets kernel attributes before any capture)
+    if (first || !cg_graph<T>(c, nrhs, dinv, w, r, d, p, q, chunk, s, &gs))
+      HDG_TRY(cg_iterations<T>(c, nrhs, dinv, w, r, d, p, q, chunk, s));
+    HDG_TRY(gs);
+    first = false;
     HDG_CUDA(cudaMemcpyAsync(hflags.data(), flags, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s));
     HDG_CUDA(cudaStreamSynchronize(s));
     bool all = true;
@@ -307,7 +440,7 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
   const int n = c->n;
   hdg_solve_opts o;
   if (opts) o = *opts;
-  else { o.tol = 1e-10; o.max_iter = 10000; o.max_outer = 20; o.inner = HDG_FP64; o.inner_tol = 0.0; }
+  else { o.tol = 1e-10; o.max_iter = 10000; o.max_outer = 20; o.inner = HDG_FP64; o.inner_tol = 0.0; o.precond = 1; }
   if (!(o.tol > 0.0) || o.max_iter < 1 || o.max_outer < 1) return fail(HDG_ERR_INVALID_ARG, "bad solve options");
   if (o.inner == HDG_BF16) return fail(HDG_ERR_UNSUPPORTED, "BF16 inner solve is not available");
   double tol_inner = o.inner_tol > 0.0 ? o.inner_tol : (o.inner == HDG_FP64 ? 0.1 * o.tol : 1e-5);
@@ -341,8 +474,8 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
     { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<double, double>(n, bdry, ghat, c->mesh.nbfaces, nrhs, B, B, c->StM, 1.0, 0, s))); }
   // 3. transformed right-hand side with Dirichlet lift and Neumann load
   {
-    HDG_TRY(zero_x23<double>(c, Fhat, nrhs, s));
-    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv);
+    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv, nrhs);
+    HDG_TRY(zero_for_tpt<double>(c, Fhat, nrhs, a.nseg, s));
     a.y = Fhat;
     a.gbd = ghat;
     a.src = fhat;
@@ -397,10 +530,10 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
     for (int r = 0; r < nrhs; ++r) caps[r] = std::max(0, o.max_iter - total_it[r]);
     // inner solve K-hat d = r-hat; d is left in W_D
     if (o.inner == HDG_FP64) {
-      HDG_TRY(inner_cg<double>(c, nrhs, lam, rhat, tol_inner, active, caps, it, st, s));
+      HDG_TRY(inner_cg<double>(c, nrhs, lam, rhat, tol_inner, active, caps, o.precond != 0, it, st, s));
       { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_to<double>(xhat, wsp<double>(c, W_D), tot, s)); }
     } else {
-      HDG_TRY(inner_cg<float>(c, nrhs, lam, rhat, tol_inner, active, caps, it, st, s));
+      HDG_TRY(inner_cg<float>(c, nrhs, lam, rhat, tol_inner, active, caps, o.precond != 0, it, st, s));
       { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_to<float>(xhat, wsp<float>(c, W_D), tot, s)); }
     }
     zero_x = false;
@@ -417,7 +550,7 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
   if (u_out) {
     HDG_TRY(ensure(c->ws[W_WVOL], sizeof(double) * (size_t)V * nrhs));
     double* w = wsp<double>(c, W_WVOL);
-    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv);
+    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv, nrhs);
     a.x = xhat;
     a.gbd = ghat;
     a.src = fhat;
@@ -471,6 +604,12 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 extern "C" {
 
 const char* hdg_last_error(void) { return g_last_error.c_str(); }
+
+hdg_status hdg_set_x1_segment(hdg_ctx* c, int elements) {
+  if (!c || elements < 0) return fail(HDG_ERR_INVALID_ARG, "NULL context or negative segment length");
+  c->seg_override = elements;
+  return HDG_OK;
+}
 
 hdg_status hdg_profile(hdg_ctx* c, int enable) {
   if (!c) return fail(HDG_ERR_INVALID_ARG, "NULL context");
@@ -652,6 +791,10 @@ void hdg_destroy(hdg_ctx* c) {
     if (b.p) cudaFree(b.p);
   for (auto& v : c->ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
+  for (DevBuf* b : {&c->pc_diag, &c->pc_w64, &c->pc_w32})
+    if (b->p) cudaFree(b->p);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
 }
 

@@ -114,9 +114,12 @@ extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_l
   if ((e = hdg::launch_face_transform<double, double>(v.n, d_x, xh, v.mesh.nfaces, nrhs, v.ntrace, v.ntrace, v.StM,
                                                       1.0, 0, s)) != cudaSuccess)
     return cuda_fail(e, "face transform in");
-  // the array keeps the previous call's contents: the x2/x3 blocks of the
-  // operator output are accumulated with atomics and must start at zero
-  const long long off = v.mesh.blk[1] * (long long)v.n * v.n;
+  int seg = 1, nseg = 1;
+  hdg::tpt_split(v.n, v.mesh.ne, nrhs, &seg, &nseg);
+  // the array keeps the previous call's contents: the parts of the operator
+  // output that are accumulated with atomics must start at zero (the x2/x3
+  // blocks, and everything when x1-pencils are split into segments)
+  const long long off = nseg > 1 ? 0 : v.mesh.blk[1] * (long long)v.n * v.n;
   if (v.ntrace - off > 0 &&
       (e = cudaMemset2DAsync(yh + off, sizeof(double) * v.ntrace, 0, sizeof(double) * (v.ntrace - off), nrhs, s)) !=
           cudaSuccess)
@@ -132,6 +135,8 @@ extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_l
   a.trace_stride = v.ntrace;
   a.ppb = hdg::tpt_ppb(v.n);
   a.npencils = (long long)v.mesh.ne[1] * v.mesh.ne[2];
+  a.seg = seg;
+  a.nseg = nseg;
   if ((e = hdg::launch_tpt<double, double>(hdg::TPT_APPLY, v.n, a, nrhs, s)) != cudaSuccess)
     return cuda_fail(e, "operator");
   if ((e = hdg::launch_face_transform<double, double>(v.n, yh, d_y, v.mesh.nfaces, nrhs, v.ntrace, v.ntrace, v.MS, 1.0,

@@ -14,10 +14,13 @@ namespace hdg {
 template <typename T, typename ST>
 cudaError_t launch_tpt(int mode, int n, TptArgs<T, ST> a, int nrhs, cudaStream_t s);
 
-// pencils per block and threads per block for degree n
+// launch geometry for degree n: segments per block (ppb), threads per block,
+// and the pencil split: `seg` elements per segment, `nseg` segments per
+// x1-pencil, chosen so that nrhs x ne[1] x ne[2] x nseg slots fill the GPU
 int tpt_ppb(int n);
 int tpt_threads(int n, int ppb);
-long long tpt_blocks(long long npencils, int ppb);
+long long tpt_blocks(long long nslots, int ppb);
+void tpt_split(int n, const int ne[3], int nrhs, int* seg, int* nseg);
 
 // ---- kernels.cu ---------------------------------------------------------------
 // y_f = scale (W (x) W) x_f for every face f (n x n nodes, lower axis fastest),
@@ -50,11 +53,19 @@ cudaError_t launch_sub(const double* a, const double* b, double* out, long long 
 template <typename T>
 cudaError_t launch_add_to(double* x, const T* d, long long count, cudaStream_t s);  // x += d
 
-// deterministic dot products a_r . b_r per right-hand side into out[r]
-// (partials[nrhs * blocks], counter[nrhs] zero on entry and exit)
+// deterministic dot products sum_i a_i b_i (w_i) per right-hand side into
+// out[r]; w may be null (partials[nrhs * blocks], counter[nrhs] zero on
+// entry and exit)
 template <typename T>
-cudaError_t launch_dot(const T* a, const T* b, long long len, int nrhs, double* partials,
+cudaError_t launch_dot(const T* a, const T* b, const T* w, long long len, int nrhs, double* partials,
                        unsigned int* counter, double* out, int blocks, cudaStream_t s);
+
+// face-block Jacobi preconditioner: diag (zeroed by the caller) += the face
+// self-coupling of K-hat; then w = 1 / diag in FP64 and FP32
+cudaError_t launch_pc_diag(const MeshDev& m, int n, const Tables<double>& tab, const double* metric,
+                           const double* dinv, long long dinv_rhs_stride, double* diag, int nrhs,
+                           long long tstride, cudaStream_t s);
+cudaError_t launch_pc_invert(const double* diag, double* w64, float* w32, long long count, cudaStream_t s);
 
 // ---- CG (cg_kernels in kernels.cu) ----------------------------------------------
 struct CgScalars {
@@ -70,15 +81,16 @@ struct CgScalars {
 // right-hand side is already masked in `flags`); flags[r] mirrors done.
 cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, double tol, int max_it,
                            int nrhs, cudaStream_t s);
-// alpha = rr / pq; d += alpha p; r -= alpha q; rr' = r.r; beta = rr'/rr; the
-// last block updates the scalars and flags[r] (no effect once done)
+// alpha = rz / pq; d += alpha p; r -= alpha q; q = 0 (ready for the next
+// operator launch); rz' = r . W r (W = w, or I if w is null); beta = rz'/rz;
+// the last block updates the scalars and flags[r] (no effect once done)
 template <typename T>
 cudaError_t launch_cg_update(CgScalars* cg, int* flags, const double* pq, T* d, T* r, const T* p,
-                             const T* q, long long len, int nrhs, double* partials,
+                             T* q, const T* w, long long len, int nrhs, double* partials,
                              unsigned int* counter, int blocks, cudaStream_t s);
-// p = r + beta p (skips finished right-hand sides)
+// p = W r + beta p (skips finished right-hand sides)
 template <typename T>
-cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, long long len, int nrhs,
+cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w, long long len, int nrhs,
                               cudaStream_t s);
 
 // ---- read-only view of a context's device tables (hdg_api.cu) ----------------

@@ -167,6 +167,62 @@ __global__ void neumann_add_kernel(MeshDev m, int n, const double* __restrict__ 
   }
 }
 
+// ---- face-block Jacobi preconditioner in the transformed basis (Sec. 5.1) ----
+// The self-coupling of a face f in K-hat is the sum over its two elements of
+// d (I (x) I (x) H) - d^2 (I (x) I (x) B_S^T) D_Z^-1 (I (x) I (x) B_S) restricted
+// to f's side s; with B_S[m][s]^2 = c_m^2 it is diagonal in the face modes:
+//   Y(a, b) = sum_e [ d h0 - d^2 sum_m c_m^2 D_Z^-1(m, a, b) ].
+__global__ void pc_diag_kernel(MeshDev m, int n, Tables<double> tab, const double* __restrict__ metric,
+                               const double* __restrict__ dinv, long long dinv_rhs_stride,
+                               double* __restrict__ diag, long long tstride) {
+  const int r = blockIdx.y;
+  const int n2 = n * n;
+  const long long n3 = (long long)n2 * n;
+  const long long nel = (long long)m.ne[0] * m.ne[1] * m.ne[2];
+  const long long total = nel * n2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long e = t / n2;
+    const int q = (int)(t - e * n2);
+    const int lo = q % n, hi = q / n;
+    const int e1 = (int)(e % m.ne[0]), e2 = (int)((e / m.ne[0]) % m.ne[1]);
+    const int e3 = (int)(e / ((long long)m.ne[0] * m.ne[1]));
+    const double* mt = metric + (m.uniform ? 0 : 4 * e);
+    const double* dz = dinv + r * dinv_rhs_stride + (m.uniform ? 0 : e * n3);
+    double sd[3] = {0.0, 0.0, 0.0};
+    for (int t2 = 0; t2 < n; ++t2) {
+      const double c2 = tab.c[t2] * tab.c[t2];
+      sd[0] += c2 * dz[t2 + n * lo + n2 * hi];   // x1 face node (j, k) = (lo, hi)
+      sd[1] += c2 * dz[lo + n * t2 + n2 * hi];   // x2 face node (i, k) = (lo, hi)
+      sd[2] += c2 * dz[lo + n * hi + n2 * t2];   // x3 face node (i, j) = (lo, hi)
+    }
+    const int ed[3] = {e1, e2, e3};
+    const long long fab[3] = {e2 + (long long)m.ne[1] * e3, e1 + (long long)m.ne[0] * e3,
+                              e1 + (long long)m.ne[0] * e2};
+    const long long pl[3] = {(long long)m.ne[1] * m.ne[2], (long long)m.ne[0] * m.ne[2],
+                             (long long)m.ne[0] * m.ne[1]};
+    for (int d = 0; d < 3; ++d) {
+      const double dd = mt[1 + d];
+      const double v = dd * tab.h0 - dd * dd * sd[d];
+      for (int s = 0; s < 2; ++s) {
+        const int plane = ed[d] + s;
+        if (plane < m.lo[d] || plane > m.hi[d]) continue;
+        red_add(diag + r * tstride + (m.blk[d] + (long long)(plane - m.lo[d]) * pl[d] + fab[d]) * n2 + q, v);
+      }
+    }
+  }
+}
+
+__global__ void pc_invert_kernel(const double* __restrict__ diag, double* __restrict__ w64,
+                                 float* __restrict__ w32, long long count) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+       t += (long long)gridDim.x * blockDim.x) {
+    const double w = 1.0 / diag[t];
+    w64[t] = w;
+    w32[t] = (float)w;
+  }
+}
+
 // ---- element-wise helpers ----------------------------------------------------------
 template <typename TI, typename TO>
 __global__ void convert_kernel(const TI* __restrict__ x, TO* __restrict__ y, long long count) {
@@ -211,8 +267,9 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
-// Writes the block partial; returns true in thread 0 of the last block to
-// finish, after which every partial of right-hand side r is visible.
+// Writes the block partial; returns true in every thread of the last block
+// to finish (block-uniform), after which every partial of right-hand side r
+// is visible.
 __device__ __forceinline__ bool finish_partial(double s, double* partials, unsigned int* counter, int r) {
   __shared__ bool last;
   if (threadIdx.x == 0) {
@@ -222,52 +279,64 @@ __device__ __forceinline__ bool finish_partial(double s, double* partials, unsig
     last = (done == gridDim.x - 1);
   }
   __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    return true;
-  }
-  return false;
+  const bool l = last;
+  if (l) __threadfence();
+  return l;
 }
 
+// Sum of the gridDim.x partials of right-hand side r by the whole (last)
+// block: fixed strided split and fixed tree, so the result is deterministic.
+// Valid in thread 0.
 __device__ __forceinline__ double sum_partials(const double* partials, int r) {
   const volatile double* pp = partials + (long long)r * gridDim.x;
-  double s = 0.0;
-  for (unsigned int b = 0; b < gridDim.x; ++b) s += pp[b];
-  return s;
+  double v = 0.0;
+  for (unsigned int b = threadIdx.x; b < gridDim.x; b += blockDim.x) v += pp[b];
+  return block_sum(v);
 }
 
 template <typename T>
-__global__ void dot_kernel(const T* __restrict__ a, const T* __restrict__ b, long long len,
-                           double* partials, unsigned int* counter, double* out) {
+__global__ void dot_kernel(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ w,
+                           long long len, double* partials, unsigned int* counter, double* out) {
   const int r = blockIdx.y;
   const T* ar = a + r * len;
   const T* br = b + r * len;
+  const T* wr = w ? w + r * len : nullptr;
   double acc = 0.0;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
-       t += (long long)gridDim.x * blockDim.x)
-    acc += static_cast<double>(ar[t]) * static_cast<double>(br[t]);
+       t += (long long)gridDim.x * blockDim.x) {
+    const double ab = static_cast<double>(ar[t]) * static_cast<double>(br[t]);
+    acc += wr ? ab * static_cast<double>(wr[t]) : ab;
+  }
   const double s = block_sum(acc);
   if (finish_partial(s, partials, counter, r)) {
-    out[r] = sum_partials(partials, r);
-    counter[r] = 0u;
+    const double tot = sum_partials(partials, r);
+    if (threadIdx.x == 0) {
+      out[r] = tot;
+      counter[r] = 0u;
+    }
   }
 }
 
 // FP32 dot: accumulate in FP32 per thread (no FP64 arithmetic in the loop)
 template <>
 __global__ void dot_kernel<float>(const float* __restrict__ a, const float* __restrict__ b,
-                                  long long len, double* partials, unsigned int* counter, double* out) {
+                                  const float* __restrict__ w, long long len, double* partials,
+                                  unsigned int* counter, double* out) {
   const int r = blockIdx.y;
   const float* ar = a + r * len;
   const float* br = b + r * len;
+  const float* wr = w ? w + r * len : nullptr;
   float acc = 0.f;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
        t += (long long)gridDim.x * blockDim.x)
-    acc = fmaf(ar[t], br[t], acc);
+    acc = fmaf(wr ? ar[t] * wr[t] : ar[t], br[t], acc);
   const double s = block_sum((double)acc);
   if (finish_partial(s, partials, counter, r)) {
-    out[r] = sum_partials(partials, r);
-    counter[r] = 0u;
+    const double tot = sum_partials(partials, r);
+    if (threadIdx.x == 0) {
+      out[r] = tot;
+      counter[r] = 0u;
+    }
   }
 }
 
@@ -293,8 +362,8 @@ __global__ void cg_init_kernel(CgScalars* cg, int* flags, const double* rr, doub
 template <typename T>
 __global__ void cg_update_kernel(CgScalars* cg, int* flags, const double* __restrict__ pq,
                                  T* __restrict__ d, T* __restrict__ rvec, const T* __restrict__ p,
-                                 const T* __restrict__ q, long long len, double* partials,
-                                 unsigned int* counter) {
+                                 T* __restrict__ q, const T* __restrict__ w, long long len,
+                                 double* partials, unsigned int* counter) {
   const int r = blockIdx.y;
   if (flags[r]) return;
   // scalars once per block: FP64 division is slow on this part
@@ -315,18 +384,21 @@ __global__ void cg_update_kernel(CgScalars* cg, int* flags, const double* __rest
   T* dr = d + r * len;
   T* rv = rvec + r * len;
   const T* pr = p + r * len;
-  const T* qr = q + r * len;
+  T* qr = q + r * len;
+  const T* wr = w ? w + r * len : nullptr;
   T acc = T(0);
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
        t += (long long)gridDim.x * blockDim.x) {
     dr[t] = fma(al, pr[t], dr[t]);
     const T rn = fma(-al, qr[t], rv[t]);
+    qr[t] = T(0);
     rv[t] = rn;
-    acc = fma(rn, rn, acc);
+    acc = fma(wr ? rn * wr[t] : rn, rn, acc);   // r . z with z = W r
   }
   const double s = block_sum(static_cast<double>(acc));
   if (finish_partial(s, partials, counter, r)) {
     const double rr_new = sum_partials(partials, r);
+    if (threadIdx.x != 0) return;
     counter[r] = 0u;
     CgScalars c = cg[r];
     c.alpha = alpha;
@@ -347,7 +419,7 @@ __global__ void cg_update_kernel(CgScalars* cg, int* flags, const double* __rest
 
 template <typename T>
 __global__ void cg_pupdate_kernel(const CgScalars* cg, T* __restrict__ p, const T* __restrict__ rvec,
-                                  long long len) {
+                                  const T* __restrict__ w, long long len) {
   const int r = blockIdx.y;
   if (cg[r].done) return;
   __shared__ T s_beta;
@@ -356,9 +428,10 @@ __global__ void cg_pupdate_kernel(const CgScalars* cg, T* __restrict__ p, const 
   const T beta = s_beta;
   T* pr = p + r * len;
   const T* rr = rvec + r * len;
+  const T* wr = w ? w + r * len : nullptr;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
        t += (long long)gridDim.x * blockDim.x)
-    pr[t] = fma(beta, pr[t], rr[t]);
+    pr[t] = fma(beta, pr[t], wr ? wr[t] * rr[t] : rr[t]);   // p = z + beta p
 }
 
 template <typename TI, typename TO, int N>
@@ -478,16 +551,31 @@ template cudaError_t launch_add_to<double>(double*, const double*, long long, cu
 template cudaError_t launch_add_to<float>(double*, const float*, long long, cudaStream_t);
 
 template <typename T>
-cudaError_t launch_dot(const T* a, const T* b, long long len, int nrhs, double* partials,
+cudaError_t launch_dot(const T* a, const T* b, const T* w, long long len, int nrhs, double* partials,
                        unsigned int* counter, double* out, int blocks, cudaStream_t s) {
   dim3 grid(blocks, nrhs);
-  dot_kernel<T><<<grid, kVecThreads, 0, s>>>(a, b, len, partials, counter, out);
+  dot_kernel<T><<<grid, kVecThreads, 0, s>>>(a, b, w, len, partials, counter, out);
   return cudaGetLastError();
 }
-template cudaError_t launch_dot<double>(const double*, const double*, long long, int, double*,
-                                        unsigned int*, double*, int, cudaStream_t);
-template cudaError_t launch_dot<float>(const float*, const float*, long long, int, double*,
+template cudaError_t launch_dot<double>(const double*, const double*, const double*, long long, int,
+                                        double*, unsigned int*, double*, int, cudaStream_t);
+template cudaError_t launch_dot<float>(const float*, const float*, const float*, long long, int, double*,
                                        unsigned int*, double*, int, cudaStream_t);
+
+cudaError_t launch_pc_diag(const MeshDev& m, int n, const Tables<double>& tab, const double* metric,
+                           const double* dinv, long long dinv_rhs_stride, double* diag, int nrhs,
+                           long long tstride, cudaStream_t s) {
+  const long long total = (long long)m.ne[0] * m.ne[1] * m.ne[2] * n * n;
+  dim3 grid(grid_for(total, kVecThreads), nrhs);
+  pc_diag_kernel<<<grid, kVecThreads, 0, s>>>(m, n, tab, metric, dinv, dinv_rhs_stride, diag, tstride);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pc_invert(const double* diag, double* w64, float* w32, long long count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  pc_invert_kernel<<<grid_for(count, kVecThreads), kVecThreads, 0, s>>>(diag, w64, w32, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, double tol, int max_it,
                            int nrhs, cudaStream_t s) {
@@ -497,29 +585,29 @@ cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, double t
 
 template <typename T>
 cudaError_t launch_cg_update(CgScalars* cg, int* flags, const double* pq, T* d, T* r, const T* p,
-                             const T* q, long long len, int nrhs, double* partials,
+                             T* q, const T* w, long long len, int nrhs, double* partials,
                              unsigned int* counter, int blocks, cudaStream_t s) {
   dim3 grid(blocks, nrhs);
-  cg_update_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, pq, d, r, p, q, len, partials, counter);
+  cg_update_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, pq, d, r, p, q, w, len, partials, counter);
   return cudaGetLastError();
 }
 template cudaError_t launch_cg_update<double>(CgScalars*, int*, const double*, double*, double*,
-                                              const double*, const double*, long long, int, double*,
-                                              unsigned int*, int, cudaStream_t);
+                                              const double*, double*, const double*, long long, int,
+                                              double*, unsigned int*, int, cudaStream_t);
 template cudaError_t launch_cg_update<float>(CgScalars*, int*, const double*, float*, float*,
-                                             const float*, const float*, long long, int, double*,
-                                             unsigned int*, int, cudaStream_t);
+                                             const float*, float*, const float*, long long, int,
+                                             double*, unsigned int*, int, cudaStream_t);
 
 template <typename T>
-cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, long long len, int nrhs,
+cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w, long long len, int nrhs,
                               cudaStream_t s) {
   dim3 grid(grid_for(len, kVecThreads), nrhs);
-  cg_pupdate_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, p, r, len);
+  cg_pupdate_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, p, r, w, len);
   return cudaGetLastError();
 }
-template cudaError_t launch_cg_pupdate<double>(const CgScalars*, double*, const double*, long long,
-                                               int, cudaStream_t);
-template cudaError_t launch_cg_pupdate<float>(const CgScalars*, float*, const float*, long long, int,
-                                              cudaStream_t);
+template cudaError_t launch_cg_pupdate<double>(const CgScalars*, double*, const double*, const double*,
+                                               long long, int, cudaStream_t);
+template cudaError_t launch_cg_pupdate<float>(const CgScalars*, float*, const float*, const float*,
+                                              long long, int, cudaStream_t);
 
 }  // namespace hdg

@@ -16,11 +16,13 @@
 // That is 7 n^3 multiply-adds per element instead of the 25 n^3 flops
 // (12 + 1 + 12 n^3) of the direct evaluation.
 //
-// Face ownership: an x1-face is shared by consecutive elements of the same
-// pencil; the thread of a face node keeps its running sum in a register and
-// stores it once.  x2/x3 faces are shared with neighbouring pencils: both
-// contributions are added with red.global.add into an output zeroed before
-// the launch (two adds onto zero commute exactly, so the result is
+// Work split: a CTA slot marches over a segment of `seg` consecutive
+// elements of one x1-pencil (n^2 threads, one per x1-line).  An x1-face
+// inside a segment is shared by consecutive elements of the slot; the thread
+// of a face node keeps its running sum in a register and stores it once.
+// x1-faces on segment ends and all x2/x3 faces are shared with other slots:
+// both contributions are added with red.global.add into an output zeroed
+// before the launch (two adds onto zero commute exactly, so the result is
 // deterministic).
 //
 // Modes:
@@ -61,8 +63,10 @@ struct TptArgs {
   const T* src;                 // f-hat volume source (RHS, RECOVER)
   T* vout;                      // w volume output (RECOVER)
   long long vol_stride;
-  int ppb;                      // pencils per block
+  int ppb;                      // pencil segments per block
   long long npencils;           // ne[1] * ne[2]
+  int seg;                      // elements per pencil segment (x1 direction)
+  int nseg;                     // segments per pencil = ceil(ne[0] / seg)
   const int* skip;              // per rhs: nonzero -> do nothing (converged), or null
   CgHook hook;                  // partials == null: no dot
 };
@@ -92,12 +96,16 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
   const int tid = threadIdx.x;
   const int slot = tid / N2;
   const int line = tid - slot * N2;
-  const long long pencil = (long long)blockIdx.x * a.ppb + slot;
+  const long long slot_id = (long long)blockIdx.x * a.ppb + slot;
+  const long long pencil = slot_id / a.nseg;
+  const int sg = (int)(slot_id - pencil * a.nseg);
   const bool act = slot < a.ppb && pencil < a.npencils;
   const MeshDev& m = a.mesh;
   const int N1e = m.ne[0], N2e = m.ne[1], N3e = m.ne[2];
   const int e2 = act ? (int)(pencil % N2e) : 0;
   const int e3 = act ? (int)(pencil / N2e) : 0;
+  const int e1s = act ? sg * a.seg : 0;
+  const int e1e = act ? min(e1s + a.seg, N1e) : 0;
 
   T* S2p = sm + (act ? slot : 0) * PER;
   T* S2m = S2p + N2;
@@ -129,16 +137,19 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
 
   T carry = T(0);
   T dot = T(0);
-  T xlo1 = act ? face_in(0, 0, f0, pl0) : T(0);
+  T xlo1 = act ? face_in(0, e1s, f0, pl0) : T(0);
 
-  for (int e1 = 0; e1 < N1e; ++e1) {
-    const long long elem = e1 + (long long)N1e * (e2 + (long long)N2e * e3);
+  // same trip count in every slot of the CTA (the loop holds barriers)
+  for (int t = 0; t < a.seg; ++t) {
+    const int e1 = e1s + t;
+    const bool live = act && e1 < e1e;
+    const long long elem = live ? e1 + (long long)N1e * (e2 + (long long)N2e * e3) : 0;
     const T* mt = a.metric + (m.uniform ? 0 : 4 * elem);
     const T d1 = mt[1], d2 = mt[2], d3 = mt[3];
     const long long f1 = e1 + (long long)N1e * e3;  // x2-face index in its plane
     const long long f2 = e1 + (long long)N1e * e2;  // x3-face index in its plane
     T xhi1 = T(0);
-    if (act) {
+    if (live) {
       xhi1 = face_in(0, e1 + 1, f0, pl0);
       const T x2l = face_in(1, e2, f1, pl1), x2h = face_in(1, e2 + 1, f1, pl1);
       const T x3l = face_in(2, e3, f2, pl2), x3h = face_in(2, e3 + 1, f2, pl2);
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
     // expansion along the x1-line (j, k) = (line % N, line / N), x1 contraction
     const T S1 = xlo1 + xhi1, D1 = xlo1 - xhi1;
     T Pp = T(0), Pm = T(0);
-    if (act) {
+    if (live) {
       const int j = line % N, k = line / N;
       const T Ap = d1 * S1, Am = d1 * D1;
       const T cjd2 = a.tab.c[j] * d2, ckd3 = a.tab.c[k] * d3;
@@ -176,7 +187,7 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
     }
     __syncthreads();
 
-    if (act) {
+    if (live) {
       const int i = line % N, mm = line / N;
       if (MODE == TPT_RECOVER) {
         // w = (f-hat - F_E) / D_Z = -u ; thread (i, mm) writes points (i, mm, k)
@@ -186,11 +197,11 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
       } else {
         T Qp = T(0), Qm = T(0), Rp = T(0), Rm = T(0);
 #pragma unroll
-        for (int t = 0; t < N; ++t) {
-          const T uq = U[i + N * t + N2 * mm];   // (i, j = t, k = mm)
-          const T ur = U[i + N * mm + N2 * t];   // (i, j = mm, k = t)
-          if (t < NE) { Qp = fma(a.tab.c[t], uq, Qp); Rp = fma(a.tab.c[t], ur, Rp); }
-          else        { Qm = fma(a.tab.c[t], uq, Qm); Rm = fma(a.tab.c[t], ur, Rm); }
+        for (int mo = 0; mo < N; ++mo) {
+          const T uq = U[i + N * mo + N2 * mm];   // (i, j = mo, k = mm)
+          const T ur = U[i + N * mm + N2 * mo];   // (i, j = mm, k = mo)
+          if (mo < NE) { Qp = fma(a.tab.c[mo], uq, Qp); Rp = fma(a.tab.c[mo], ur, Rp); }
+          else         { Qm = fma(a.tab.c[mo], uq, Qm); Rm = fma(a.tab.c[mo], ur, Rm); }
         }
         const T hs = a.tab.h0 + a.tab.h1, hd = a.tab.h0 - a.tab.h1;
         const T sgn = (MODE == TPT_RHS) ? T(-1) : T(1);
@@ -220,11 +231,20 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
           const T sum = d1 * (hs * S1 - two * Pp), dif = d1 * (hd * D1 - two * Pm);
           const T rlo = sgn * half * (sum + dif), rhi = sgn * half * (sum - dif);
           if (MODE == TPT_APPLY) dot = fma(S1, sum, fma(D1, dif, dot));
-          if (unknown(0, e1))
-            store_from<ST, T>(yout + (m.blk[0] + (long long)(e1 - m.lo[0]) * pl0 + f0) * N2 + line, carry + rlo);
+          // plane e1: inside the segment -> complete sum, store; segment start
+          // -> shared with the previous segment (add), unless physical boundary
+          if (unknown(0, e1)) {
+            ST* dst = yout + (m.blk[0] + (long long)(e1 - m.lo[0]) * pl0 + f0) * N2 + line;
+            if (t > 0) store_from<ST, T>(dst, carry + rlo);
+            else if (e1 == 0) store_from<ST, T>(dst, rlo);
+            else red_add(dst, rlo);
+          }
           carry = rhi;
-          if (e1 == N1e - 1 && unknown(0, N1e))
-            store_from<ST, T>(yout + (m.blk[0] + (long long)(N1e - m.lo[0]) * pl0 + f0) * N2 + line, carry);
+          if (e1 == e1e - 1 && unknown(0, e1e)) {
+            ST* dst = yout + (m.blk[0] + (long long)(e1e - m.lo[0]) * pl0 + f0) * N2 + line;
+            if (e1e == N1e) store_from<ST, T>(dst, carry);
+            else red_add(dst, carry);
+          }
         }
       }
     }
@@ -234,27 +254,36 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
 
   if (MODE == TPT_APPLY && a.hook.partials != nullptr) {
     // x^T y = sum over element faces of x . r = 1/2 sum (S sum + D dif)
-    __shared__ T wsum[16];
-    T v = warp_sum(act ? dot : T(0));
-    if ((tid & 31) == 0) wsum[tid >> 5] = v;
-    __syncthreads();
+    __shared__ double wsum[16];
     __shared__ bool last;
+    T v = warp_sum(act ? dot : T(0));
+    if ((tid & 31) == 0) wsum[tid >> 5] = (double)v;
+    __syncthreads();
     if (tid == 0) {
-      T s = T(0);
+      double s = 0.0;
       for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) s += wsum[w];
-      a.hook.partials[(long long)rhs * gridDim.x + blockIdx.x] = 0.5 * (double)s;
+      a.hook.partials[(long long)rhs * gridDim.x + blockIdx.x] = 0.5 * s;
       __threadfence();
       const unsigned int done = atomicAdd(a.hook.counter + rhs, 1u);
       last = (done == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && tid == 0) {
+    if (last) {
+      // the last block sums all partials: fixed strided split + fixed tree
       __threadfence();
       const volatile double* pp = a.hook.partials + (long long)rhs * gridDim.x;
       double s = 0.0;
-      for (unsigned int b = 0; b < gridDim.x; ++b) s += pp[b];
-      a.hook.pq[rhs] = s;
-      a.hook.counter[rhs] = 0u;
+      for (unsigned int b = tid; b < gridDim.x; b += blockDim.x) s += pp[b];
+      s = warp_sum(s);
+      __syncthreads();
+      if ((tid & 31) == 0) wsum[tid >> 5] = s;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += wsum[w];
+        a.hook.pq[rhs] = t;
+        a.hook.counter[rhs] = 0u;
+      }
     }
   }
 }

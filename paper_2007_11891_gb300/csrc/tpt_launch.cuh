@@ -17,7 +17,8 @@ cudaError_t tpt_launch_one(const TptArgs<T, ST>& a, int nrhs, cudaStream_t s) {
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((unsigned)tpt_blocks(a.npencils, a.ppb), (unsigned)nrhs);
+  if (a.seg < 1 || a.nseg < 1) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)tpt_blocks(a.npencils * a.nseg, a.ppb), (unsigned)nrhs);
   tpt_kernel<T, ST, N, MODE><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -69,6 +69,10 @@ class HDG:
         except Exception:
             pass
 
+    def set_x1_segment(self, elements):
+        """Operator-kernel tuning: x1-segment length (0 = automatic)."""
+        _capi.check(_capi.lib().hdg_set_x1_segment(self._h, int(elements)), "hdg_set_x1_segment")
+
     # -- measurement -------------------------------------------------------------
     KERNEL_CLASSES = {"op_fp32": 0, "op_fp64": 1, "face": 2, "volume": 3, "rhs_recover": 4, "vector": 5}
 
@@ -107,13 +111,14 @@ class HDG:
         return y.reshape(x.shape)
 
     # -- solve -----------------------------------------------------------------
-    def _opts(self, tol, inner, max_iter, max_outer, inner_tol):
+    def _opts(self, tol, inner, max_iter, max_outer, inner_tol, precond=True):
         return _capi.HdgSolveOpts(float(tol), int(max_iter), int(max_outer), _capi.PRECISION[inner],
-                                  float(inner_tol))
+                                  float(inner_tol), int(bool(precond)))
 
     def solve(self, f, lam, bdry=None, x0=None, tol=1e-10, inner="fp32", max_iter=50000,
-              max_outer=40, inner_tol=0.0, return_u=True, check=True):
+              max_outer=40, inner_tol=0.0, return_u=True, check=True, precond=True):
         """Solve K ut = F for nodal loads f ((V,) or (nrhs, V), float64).
+        precond: face-block Jacobi preconditioner (Sec. 5.1) in the inner CG.
         Returns (traces, u or None, list of info dicts)."""
         f2 = f.reshape(-1, self.volume_size).contiguous()
         nrhs = f2.shape[0]
@@ -124,7 +129,7 @@ class HDG:
         b = None if bdry is None else bdry.reshape(nrhs, self.boundary_size).contiguous()
         x = None if x0 is None else x0.reshape(nrhs, self.trace_size).contiguous()
         info = (_capi.HdgSolveInfo * nrhs)()
-        opts = self._opts(tol, inner, max_iter, max_outer, inner_tol)
+        opts = self._opts(tol, inner, max_iter, max_outer, inner_tol, precond)
         st = _capi.lib().hdg_solve(self._h, nrhs, _lams(lam, nrhs), ctypes.c_void_p(f2.data_ptr()),
                                    ctypes.c_void_p(b.data_ptr() if b is not None else 0),
                                    ctypes.c_void_p(x.data_ptr() if x is not None else 0),

@@ -131,3 +131,20 @@ def test_apply_full_size_sampled(workload):
     assert np.abs(y[dofs] - ref).max() <= 1e-12 * np.abs(ref).max()
     y32 = h.apply(torch.tensor(x, device="cuda", dtype=torch.float32), lam).double().cpu().numpy()
     assert np.abs(y32[dofs] - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_x1_segment_length_does_not_change_results():
+    from paper_2007_11891_gb300 import HDG
+    ne, p = (7, 3, 2), 4
+    h = HDG(ne, _grid(ne, True, 5), (1, 0, 0, 0, 0, 1), p, 25.0)
+    pr = Problem(ne, _grid(ne, True, 5), (1, 0, 0, 0, 0, 1), p, 25.0, 0.9)
+    x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 8), device="cuda")
+    outs = []
+    for seg in (0, 1, 2, 3, 7, 100):
+        h.set_x1_segment(seg)
+        outs.append((h.apply(x, 0.9), h.apply(x, 0.9, basis="transformed"), h.apply(x.float(), 0.9)))
+    for o in outs[1:]:
+        for a, b in zip(o, outs[0]):
+            assert torch.equal(a, b)
+    ref = pr.apply(x.cpu().numpy())
+    assert np.abs(outs[0][0].cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()

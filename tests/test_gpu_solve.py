@@ -154,3 +154,19 @@ def test_autograd_function():
     gf, gl, _ = h.solve_adjoint(u.detach(), 2.0 * u.detach(), [2.0], tol=1e-12, inner="fp64")
     assert torch.allclose(f.grad, gf, rtol=1e-9, atol=1e-12 * float(gf.abs().max()))
     assert torch.allclose(lam.grad, gl, rtol=1e-9)
+
+
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+def test_unpreconditioned_and_preconditioned_agree(inner):
+    from paper_2007_11891_gb300 import HDG
+    ne, p, lam = (4, 4, 3), 3, 2.0
+    grid = _stretched(ne, 23)
+    h = HDG(ne, grid, (0,) * 6, p, 25.0)
+    pr = Problem(ne, grid, (0,) * 6, p, 25.0, lam)
+    f = hdg_inputs.gaussian(h.volume_size, 7)
+    ft = torch.tensor(f, device="cuda")
+    t0, _, i0 = h.solve(ft, lam, tol=1e-10, inner=inner, precond=False, return_u=False)
+    t1, _, i1 = h.solve(ft, lam, tol=1e-10, inner=inner, precond=True, return_u=False)
+    assert i1[0]["iterations"] < i0[0]["iterations"]
+    for t in (t0, t1):
+        assert _oracle_residual(pr, t.cpu().numpy(), f=f) <= 1e-10
