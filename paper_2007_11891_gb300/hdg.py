@@ -73,6 +73,11 @@ class HDG:
         """Operator-kernel tuning: x1-segment length (0 = automatic)."""
         _capi.check(_capi.lib().hdg_set_x1_segment(self._h, int(elements)), "hdg_set_x1_segment")
 
+    def set_dz_mode(self, mode):
+        """FP32 operator tuning: D_Z^-1 from 'auto', 'table' or 'kernel'."""
+        code = {"auto": 0, "table": 1, "kernel": 2}[mode]
+        _capi.check(_capi.lib().hdg_set_dz_mode(self._h, code), "hdg_set_dz_mode")
+
     # -- measurement -------------------------------------------------------------
     KERNEL_CLASSES = {"op_fp32": 0, "op_fp64": 1, "face": 2, "volume": 3, "rhs_recover": 4, "vector": 5}
 

@@ -148,3 +148,22 @@ def test_x1_segment_length_does_not_change_results():
             assert torch.equal(a, b)
     ref = pr.apply(x.cpu().numpy())
     assert np.abs(outs[0][0].cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("stretched", [True, False])
+def test_fp32_dz_table_and_in_kernel_agree(stretched):
+    from paper_2007_11891_gb300 import HDG
+    ne, p, lam = (5, 4, 3), 6, 3.0
+    grid = _grid(ne, stretched, 12)
+    h = HDG(ne, grid, (0, 0, 1, 0, 0, 0), p, 25.0)
+    ref = Problem(ne, grid, (0, 0, 1, 0, 0, 0), p, 25.0, lam).apply(hdg_inputs.uniform_pm1(h.trace_size, 3))
+    x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 3), device="cuda", dtype=torch.float32)
+    for mode in ("table", "kernel", "auto"):
+        h.set_dz_mode(mode)
+        for basis in ("nodal",):
+            y = h.apply(x, lam, basis=basis).double().cpu().numpy()
+            assert np.abs(y - ref).max() <= 1e-5 * np.abs(ref).max(), mode
+    h.set_dz_mode("kernel")
+    f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 4), device="cuda")
+    _, _, info = h.solve(f, lam, tol=1e-10, inner="fp32", return_u=False)
+    assert info[0]["status"] == "OK" and info[0]["rel_residual"] <= 1e-10
