@@ -165,8 +165,8 @@ hdg_status hdg_apply(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_precisi
  *
  * Its temporaries (the face-eigenbasis traces before and after the
  * operator, 2 x nrhs x hdg_trace_size() doubles, and the D_Z^-1 tables of
- * the lambdas, nrhs x n^3 doubles on a uniform grid or nrhs x n_e x n^3 on a
- * stretched one) live in one static device array of 2^21 doubles (16 MiB),
+ * the lambdas, nrhs x n^2 x (n rounded up to even) doubles on a uniform
+ * grid, n_e times that on a stretched one) live in one static device array of 2^21 doubles (16 MiB),
  * which every GPU that loads the library reserves until the process exits.
  * Larger requests are rejected with HDG_ERR_INVALID_ARG and a message
  * giving the size needed (use hdg_apply then).
@@ -215,6 +215,13 @@ hdg_status hdg_solve_adjoint(hdg_ctx* ctx, int nrhs, const double* h_lambda, con
  * the GPU).  Speed only: every value gives bitwise identical results.
  * Errors: INVALID_ARG (NULL context, negative length).                    */
 hdg_status hdg_set_x1_segment(hdg_ctx* ctx, int elements);
+
+/* Tuning (not part of the method): where the FP32 operator takes the
+ * inverse eigenvalue scaling D_Z^-1 of Sec. 4.1 from.  0 automatic (a table
+ * when it fits in L2, else computed in the kernel), 1 always the table,
+ * 2 always computed in the kernel (FP32 only; FP64 always uses the table).
+ * Results agree to FP32 rounding.  Errors: INVALID_ARG.                    */
+hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
 
 /* Measurement support (not part of the method).  Kernel classes:
  *   0 condensed operator, FP32 arithmetic   1 condensed operator, FP64

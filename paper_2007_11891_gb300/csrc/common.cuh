@@ -26,14 +26,49 @@ struct MeshDev {
 template <typename T>
 struct Tables {
   T c[kMaxNDev];
+  T lam[kMaxNDev];   // Lambda_m (used when D_Z^-1 is computed in the kernel)
   T h0, h1;
 };
+
+// 16-byte vector type per arithmetic type and the padded row length used by
+// the operator's shared-memory arrays and by the D_Z^-1 tables: rows of n
+// values are padded to a multiple of the vector width so that a row can be
+// read with 16-byte accesses.
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using type = float4;
+  static constexpr int L = 4;
+};
+template <>
+struct Vec<double> {
+  using type = double2;
+  static constexpr int L = 2;
+};
+__host__ __device__ constexpr int dz_row(int n, int elem_bytes) {
+  return elem_bytes == 4 ? (n + 3) / 4 * 4 : (n + 1) / 2 * 2;
+}
+__device__ __forceinline__ float vget(const float4& v, int l) { return l == 0 ? v.x : l == 1 ? v.y : l == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vget(const double2& v, int l) { return l == 0 ? v.x : v.y; }
+__device__ __forceinline__ void vset(float4& v, int l, float x) {
+  if (l == 0) v.x = x; else if (l == 1) v.y = x; else if (l == 2) v.z = x; else v.w = x;
+}
+__device__ __forceinline__ void vset(double2& v, int l, double x) {
+  if (l == 0) v.x = x; else v.y = x;
+}
 
 // n x n matrix passed by value (row-major).
 template <typename T>
 struct Mat1D {
   T a[kMaxNDev * kMaxNDev];
 };
+
+// 1 / x for the in-kernel D_Z^-1: the hardware reciprocal approximation in
+// FP32 (relative error ~2^-22, below the FP32 rounding of the operator
+// itself); exact division in FP64.
+__device__ __forceinline__ float dz_recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double dz_recip(double x) { return 1.0 / x; }
 
 // ---- storage conversions --------------------------------------------------
 template <typename ST, typename T>

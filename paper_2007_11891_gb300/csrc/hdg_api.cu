@@ -60,7 +60,7 @@ struct hdg_ctx {
   hdg::Mat1D<double> StM, MS, S, St, M;
   // D_Z^-1 tables for the lambdas of the last call, per precision
   std::vector<double> lam64, lam32;
-  DevBuf dinv64, dinv32, lam_dev;
+  DevBuf dinv64, dinv32, lam_dev64, lam_dev32;
   // workspaces
   DevBuf ws[24];
   DevBuf partials, counters, cgs, flags, scal;
@@ -83,6 +83,7 @@ struct hdg_ctx {
   bool capturing = false;
   int graphs_enabled = 1;
   int seg_override = 0;   // x1 segment length; 0 = automatic
+  int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
 };
 
 namespace {
@@ -154,25 +155,48 @@ template <>
 const hdg::Tables<float>& tables<float>(const hdg_ctx* c) { return c->tab32; }
 
 long long nclass(const hdg_ctx* c) { return c->uniform ? 1 : c->nelem; }
-long long n3(const hdg_ctx* c) { return (long long)c->n * c->n * c->n; }
+// entries of one D_Z^-1 table (n^2 rows of the padded row length)
+template <typename T>
+long long dz_table(const hdg_ctx* c) { return (long long)c->n * c->n * hdg::dz_row(c->n, sizeof(T)); }
 
-// D_Z^-1 tables for the given lambdas (rebuilt when they change)
+// D_Z^-1 is computed inside the FP32 operator kernel on stretched grids whose
+// per-element table would not stay resident in L2 next to the CG vectors
+// (beyond 24 MB the table costs more HBM traffic than the traces); FP64
+// kernels (bound by the FP64 pipe, where a division costs more than a load),
+// uniform grids (one small table) and small stretched grids read tables.
+constexpr size_t kDzTableL2Bytes = 24u << 20;
+template <typename T>
+bool dz_in_kernel(const hdg_ctx* c) {
+  if (sizeof(T) != 4 || c->dz_mode == 1) return false;
+  if (c->dz_mode == 2) return true;
+  return !c->uniform && (size_t)nclass(c) * dz_table<T>(c) * sizeof(T) > kDzTableL2Bytes;
+}
+
+// lambdas on the device, per precision (kept while they do not change)
+template <typename T>
+DevBuf& lam_buf(hdg_ctx* c) { return sizeof(T) == 8 ? c->lam_dev64 : c->lam_dev32; }
+
+// D_Z^-1 tables for the given lambdas (rebuilt when they change); *out is
+// null when the kernel computes D_Z^-1 itself.
 template <typename T>
 hdg_status ensure_dinv(hdg_ctx* c, int nrhs, const double* lam, cudaStream_t s, const T** out) {
   std::vector<double>& cur = sizeof(T) == 8 ? c->lam64 : c->lam32;
   DevBuf& buf = sizeof(T) == 8 ? c->dinv64 : c->dinv32;
+  DevBuf& lb = lam_buf<T>(c);
   std::vector<double> want(lam, lam + nrhs);
   if (cur != want) {
-    HDG_TRY(ensure(buf, sizeof(T) * (size_t)nrhs * nclass(c) * n3(c)));
-    HDG_TRY(ensure(c->lam_dev, sizeof(double) * nrhs));
-    HDG_CUDA(cudaMemcpyAsync(c->lam_dev.p, lam, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
-    HDG_CUDA(hdg::launch_dinv<T>(c->n, static_cast<double*>(c->lam_dev.p), nrhs, c->d_metric64, nclass(c),
-                                 c->d_Lambda, static_cast<T*>(buf.p), s));
-    // the lambda buffer is reused by later calls: finish the table first
+    HDG_TRY(ensure(lb, sizeof(double) * nrhs));
+    HDG_CUDA(cudaMemcpyAsync(lb.p, lam, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+    if (!dz_in_kernel<T>(c)) {
+      HDG_TRY(ensure(buf, sizeof(T) * (size_t)nrhs * nclass(c) * dz_table<T>(c)));
+      HDG_CUDA(hdg::launch_dinv<T>(c->n, static_cast<double*>(lb.p), nrhs, c->d_metric64, nclass(c),
+                                   c->d_Lambda, static_cast<T*>(buf.p), s));
+    }
+    // the host lambda array may change after return: finish the copy first
     HDG_CUDA(cudaStreamSynchronize(s));
     cur = want;
   }
-  *out = static_cast<const T*>(buf.p);
+  *out = dz_in_kernel<T>(c) ? nullptr : static_cast<const T*>(buf.p);
   return HDG_OK;
 }
 
@@ -183,7 +207,8 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs) {
   a.tab = tables<T>(c);
   a.metric = metric_ptr<T>(c);
   a.dinv = dinv;
-  a.dinv_rhs_stride = nclass(c) * n3(c);
+  a.dinv_rhs_stride = nclass(c) * dz_table<T>(c);
+  a.lam = static_cast<const double*>(lam_buf<T>(const_cast<hdg_ctx*>(c)).p);
   a.trace_stride = c->ntrace;
   a.bdry_stride = c->nbdry;
   a.vol_stride = c->nvol;
@@ -273,7 +298,7 @@ hdg_status ensure_pc(hdg_ctx* c, int nrhs, const double* lam, cudaStream_t s) {
   HDG_TRY(ensure(c->pc_w32, sizeof(float) * tot));
   HDG_CUDA(cudaMemsetAsync(c->pc_diag.p, 0, sizeof(double) * tot, s));
   { Timed t_(c, K_VEC, s);
-    HDG_CUDA(hdg::launch_pc_diag(c->mesh, c->n, c->tab64, c->d_metric64, dinv, nclass(c) * n3(c),
+    HDG_CUDA(hdg::launch_pc_diag(c->mesh, c->n, c->tab64, c->d_metric64, dinv, nclass(c) * dz_table<double>(c),
                                  static_cast<double*>(c->pc_diag.p), nrhs, c->ntrace, s)); }
   { Timed t_(c, K_VEC, s);
     HDG_CUDA(hdg::launch_pc_invert(static_cast<double*>(c->pc_diag.p), static_cast<double*>(c->pc_w64.p),
@@ -318,7 +343,8 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
               cudaStream_t s, hdg_status* st) {
   *st = HDG_OK;
   if (!c->graphs_enabled || c->prof_on) return false;
-  std::vector<uintptr_t> key = {sizeof(T), (uintptr_t)nrhs, (uintptr_t)dinv, (uintptr_t)w, (uintptr_t)r,
+  std::vector<uintptr_t> key = {sizeof(T), (uintptr_t)nrhs, (uintptr_t)dinv, (uintptr_t)lam_buf<T>(c).p,
+                                (uintptr_t)w, (uintptr_t)r,
                                 (uintptr_t)d, (uintptr_t)p, (uintptr_t)q, (uintptr_t)c->flags.p,
                                 (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p, (uintptr_t)c->partials.p,
                                 (uintptr_t)c->counters.p, (uintptr_t)count};
@@ -611,6 +637,13 @@ hdg_status hdg_set_x1_segment(hdg_ctx* c, int elements) {
   return HDG_OK;
 }
 
+hdg_status hdg_set_dz_mode(hdg_ctx* c, int mode) {
+  if (!c || mode < 0 || mode > 2) return fail(HDG_ERR_INVALID_ARG, "NULL context or D_Z mode outside 0..2");
+  if (mode != c->dz_mode) c->lam32.clear();   // rebuild (or drop) the FP32 table on next use
+  c->dz_mode = mode;
+  return HDG_OK;
+}
+
 hdg_status hdg_profile(hdg_ctx* c, int enable) {
   if (!c) return fail(HDG_ERR_INVALID_ARG, "NULL context");
   if (enable) {
@@ -717,6 +750,10 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int p, const hdg_options* opts, hdg_c
   c->ntrace = m.nfaces * n * n;
   c->nvol = c->nelem * n * n * n;
   c->nbdry = m.nbfaces * n * n;
+  if (c->ntrace >= (1LL << 31) || c->nbdry >= (1LL << 31) || c->nvol >= (1LL << 40)) {
+    hdg_destroy(c);
+    return fail(HDG_ERR_UNSUPPORTED, "mesh too large: the trace vector per right-hand side must stay below 2^31 values");
+  }
   // uniform: every direction has constant width (to round-off) -> one element class
   bool uni = true;
   for (int d = 0; d < 3; ++d)
@@ -760,6 +797,8 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int p, const hdg_options* opts, hdg_c
   for (int i = 0; i < n; ++i) {
     c->tab64.c[i] = c->s1.bs[i];
     c->tab32.c[i] = (float)c->s1.bs[i];
+    c->tab64.lam[i] = c->s1.Lambda[i];
+    c->tab32.lam[i] = (float)c->s1.Lambda[i];
   }
   c->tab64.h0 = c->s1.h0;
   c->tab64.h1 = c->s1.h1;
@@ -785,7 +824,8 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_metric32);
   cudaFree(c->d_Lambda);
   cudaFree(c->d_widths);
-  for (DevBuf* b : {&c->dinv64, &c->dinv32, &c->lam_dev, &c->partials, &c->counters, &c->cgs, &c->flags, &c->scal})
+  for (DevBuf* b : {&c->dinv64, &c->dinv32, &c->lam_dev64, &c->lam_dev32, &c->partials, &c->counters, &c->cgs,
+                    &c->flags, &c->scal})
     if (b->p) cudaFree(b->p);
   for (DevBuf& b : c->ws)
     if (b.p) cudaFree(b.p);

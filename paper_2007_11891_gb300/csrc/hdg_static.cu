@@ -76,9 +76,9 @@ extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_l
       hdg::set_last_error("hdg_apply_static: lambda must be finite and >= 0");
       return HDG_ERR_INVALID_ARG;
     }
-  const long long n3 = (long long)v.n * v.n * v.n;
+  const long long dzt = (long long)v.n * v.n * hdg::dz_row(v.n, sizeof(double));   // one D_Z^-1 table
   const long long trace = round_up((long long)nrhs * v.ntrace);
-  const long long table = round_up((long long)nrhs * v.nclass * n3);
+  const long long table = round_up((long long)nrhs * v.nclass * dzt);
   const long long need = 2 * trace + table + round_up(nrhs);
   if (need > (long long)kStaticScratchDoubles) {
     hdg::set_last_error(("hdg_apply_static: needs " + std::to_string(need) + " doubles of static scratch, the maximum is " +
@@ -129,7 +129,7 @@ extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_l
   a.tab = v.tab;
   a.metric = v.metric64;
   a.dinv = dinv;
-  a.dinv_rhs_stride = v.nclass * n3;
+  a.dinv_rhs_stride = v.nclass * dzt;
   a.x = xh;
   a.y = yh;
   a.trace_stride = v.ntrace;

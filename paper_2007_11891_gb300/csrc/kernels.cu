@@ -16,6 +16,34 @@ inline unsigned int grid_for(long long count, int threads, long long cap = 152LL
   return (unsigned int)b;
 }
 
+// ---- 4-wide vector access (16-byte transactions) ---------------------------------
+// Streaming kernels load every operand of a group of 4 consecutive entries
+// before storing anything, so the loads of a group are all in flight at
+// once; the group path needs 16-byte aligned rows (length % 4 == 0).
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T v[4]);
+template <>
+__device__ __forceinline__ void ld4<float>(const float* p, float v[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(const double* p, double v[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <typename T>
+__device__ __forceinline__ void st4(T* p, const T v[4]);
+template <>
+__device__ __forceinline__ void st4<float>(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void st4<double>(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+
 // ---- face transforms: y_f = scale (W (x) W) x_f (Sec. 4.2 basis change) ------
 template <typename TI, typename TO, int N>
 __global__ void face_transform_kernel(const TI* __restrict__ x, TO* __restrict__ y, long long nfaces,
@@ -123,18 +151,24 @@ __global__ void volume_transform_kernel(const double* __restrict__ x, double* __
 }
 
 // ---- D_Z^-1 tables (Sec. 4.1, fast diagonalisation) -------------------------------
+// Layout: [rhs][class][k][j][i], rows of dz_row(n) entries (padding = 0).
 template <typename T>
 __global__ void dinv_kernel(int n, const double* __restrict__ lam, int nrhs,
                             const double* __restrict__ metric, long long nclass,
                             const double* __restrict__ Lambda, T* __restrict__ out) {
-  const long long n3 = (long long)n * n * n;
-  const long long total = (long long)nrhs * nclass * n3;
+  const int row = dz_row(n, sizeof(T));
+  const long long per = (long long)n * n * row;
+  const long long total = (long long)nrhs * nclass * per;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const long long p = t % n3;
-    const long long cls = (t / n3) % nclass;
-    const int r = (int)(t / (n3 * nclass));
-    const int i = (int)(p % n), j = (int)((p / n) % n), k = (int)(p / (n * n));
+    const long long pidx = t % per;
+    const long long cls = (t / per) % nclass;
+    const int r = (int)(t / (per * nclass));
+    const int i = (int)(pidx % row), j = (int)((pidx / row) % n), k = (int)(pidx / ((long long)row * n));
+    if (i >= n) {
+      out[t] = T(0);
+      continue;
+    }
     const double* mt = metric + 4 * cls;
     const double dz = lam[r] * mt[0] + mt[1] * Lambda[i] + mt[2] * Lambda[j] + mt[3] * Lambda[k];
     out[t] = static_cast<T>(1.0 / dz);
@@ -177,7 +211,6 @@ __global__ void pc_diag_kernel(MeshDev m, int n, Tables<double> tab, const doubl
                                double* __restrict__ diag, long long tstride) {
   const int r = blockIdx.y;
   const int n2 = n * n;
-  const long long n3 = (long long)n2 * n;
   const long long nel = (long long)m.ne[0] * m.ne[1] * m.ne[2];
   const long long total = nel * n2;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -188,13 +221,14 @@ __global__ void pc_diag_kernel(MeshDev m, int n, Tables<double> tab, const doubl
     const int e1 = (int)(e % m.ne[0]), e2 = (int)((e / m.ne[0]) % m.ne[1]);
     const int e3 = (int)(e / ((long long)m.ne[0] * m.ne[1]));
     const double* mt = metric + (m.uniform ? 0 : 4 * e);
-    const double* dz = dinv + r * dinv_rhs_stride + (m.uniform ? 0 : e * n3);
+    const int row = dz_row(n, sizeof(double));
+    const double* dz = dinv + r * dinv_rhs_stride + (m.uniform ? 0 : e * (long long)n2 * row);
     double sd[3] = {0.0, 0.0, 0.0};
     for (int t2 = 0; t2 < n; ++t2) {
       const double c2 = tab.c[t2] * tab.c[t2];
-      sd[0] += c2 * dz[t2 + n * lo + n2 * hi];   // x1 face node (j, k) = (lo, hi)
-      sd[1] += c2 * dz[lo + n * t2 + n2 * hi];   // x2 face node (i, k) = (lo, hi)
-      sd[2] += c2 * dz[lo + n * hi + n2 * t2];   // x3 face node (i, j) = (lo, hi)
+      sd[0] += c2 * dz[t2 + row * (lo + n * hi)];   // x1 face node (j, k) = (lo, hi)
+      sd[1] += c2 * dz[lo + row * (t2 + n * hi)];   // x2 face node (i, k) = (lo, hi)
+      sd[2] += c2 * dz[lo + row * (hi + n * t2)];   // x3 face node (i, j) = (lo, hi)
     }
     const int ed[3] = {e1, e2, e3};
     const long long fab[3] = {e2 + (long long)m.ne[1] * e3, e1 + (long long)m.ne[0] * e3,
@@ -381,19 +415,41 @@ __global__ void cg_update_kernel(CgScalars* cg, int* flags, const double* __rest
   const bool bad = s_bad;
   const double alpha = s_alpha;
   const T al = s_al;
-  T* dr = d + r * len;
-  T* rv = rvec + r * len;
-  const T* pr = p + r * len;
-  T* qr = q + r * len;
-  const T* wr = w ? w + r * len : nullptr;
+  T* __restrict__ dr = d + r * len;
+  T* __restrict__ rv = rvec + r * len;
+  const T* __restrict__ pr = p + r * len;
+  T* __restrict__ qr = q + r * len;
+  const T* __restrict__ wr = w ? w + r * len : nullptr;
   T acc = T(0);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
-       t += (long long)gridDim.x * blockDim.x) {
-    dr[t] = fma(al, pr[t], dr[t]);
-    const T rn = fma(-al, qr[t], rv[t]);
-    qr[t] = T(0);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nvec = (len % 4 == 0) ? len / 4 : 0;
+  for (long long v = tid; v < nvec; v += stride) {
+    const long long t = 4 * v;
+    T pv[4], dv[4], qv[4], rn[4], wv[4] = {T(1), T(1), T(1), T(1)};
+    const T zero[4] = {T(0), T(0), T(0), T(0)};
+    ld4(pr + t, pv);
+    ld4(dr + t, dv);
+    ld4(qr + t, qv);
+    ld4(rv + t, rn);
+    if (wr) ld4(wr + t, wv);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      dv[k] = fma(al, pv[k], dv[k]);
+      rn[k] = fma(-al, qv[k], rn[k]);
+      acc = fma(rn[k] * wv[k], rn[k], acc);   // r . z with z = W r
+    }
+    st4(dr + t, dv);
+    st4(rv + t, rn);
+    st4(qr + t, zero);
+  }
+  for (long long t = nvec * 4 + tid; t < len; t += stride) {
+    const T pv = pr[t], dv = dr[t], qv = qr[t], r0 = rv[t], wv = wr ? wr[t] : T(1);
+    const T rn = fma(-al, qv, r0);
+    dr[t] = fma(al, pv, dv);
     rv[t] = rn;
-    acc = fma(wr ? rn * wr[t] : rn, rn, acc);   // r . z with z = W r
+    qr[t] = T(0);
+    acc = fma(rn * wv, rn, acc);
   }
   const double s = block_sum(static_cast<double>(acc));
   if (finish_partial(s, partials, counter, r)) {
@@ -426,12 +482,26 @@ __global__ void cg_pupdate_kernel(const CgScalars* cg, T* __restrict__ p, const 
   if (threadIdx.x == 0) s_beta = static_cast<T>(cg[r].beta);
   __syncthreads();
   const T beta = s_beta;
-  T* pr = p + r * len;
-  const T* rr = rvec + r * len;
-  const T* wr = w ? w + r * len : nullptr;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len;
-       t += (long long)gridDim.x * blockDim.x)
-    pr[t] = fma(beta, pr[t], wr ? wr[t] * rr[t] : rr[t]);   // p = z + beta p
+  T* __restrict__ pr = p + r * len;
+  const T* __restrict__ rr = rvec + r * len;
+  const T* __restrict__ wr = w ? w + r * len : nullptr;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nvec = (len % 4 == 0) ? len / 4 : 0;
+  for (long long v = tid; v < nvec; v += stride) {
+    const long long t = 4 * v;
+    T pv[4], rv[4], wv[4] = {T(1), T(1), T(1), T(1)};
+    ld4(pr + t, pv);
+    ld4(rr + t, rv);
+    if (wr) ld4(wr + t, wv);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) pv[k] = fma(beta, pv[k], wv[k] * rv[k]);   // p = z + beta p
+    st4(pr + t, pv);
+  }
+  for (long long t = nvec * 4 + tid; t < len; t += stride) {
+    const T z = wr ? wr[t] * rr[t] : rr[t];
+    pr[t] = fma(beta, pr[t], z);
+  }
 }
 
 template <typename TI, typename TO, int N>
@@ -504,7 +574,7 @@ cudaError_t launch_volume_transform(int n, const double* x, double* y, long long
 template <typename T>
 cudaError_t launch_dinv(int n, const double* lambda_dev, int nrhs, const double* metric,
                         long long nclass, const double* Lambda_dev, T* out, cudaStream_t s) {
-  const long long total = (long long)nrhs * nclass * n * n * n;
+  const long long total = (long long)nrhs * nclass * n * n * dz_row(n, sizeof(T));
   dinv_kernel<T><<<grid_for(total, kVecThreads), kVecThreads, 0, s>>>(n, lambda_dev, nrhs, metric,
                                                                       nclass, Lambda_dev, out);
   return cudaGetLastError();

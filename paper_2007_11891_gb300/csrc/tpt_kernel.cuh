@@ -53,8 +53,10 @@ struct TptArgs {
   MeshDev mesh;
   Tables<T> tab;
   const T* metric;              // (d0, d1, d2, d3) per element, or one entry if uniform
-  const T* dinv;                // D_Z^-1: n^3 per element (or one table if uniform)
+  const T* dinv;                // D_Z^-1: n^3 per element (or one table if uniform);
+                                // null: computed in the kernel from lam and Lambda
   long long dinv_rhs_stride;    // per right-hand side
+  const double* lam;            // per right-hand side lambda (when dinv is null)
   const ST* x;                  // unknown-face inputs (APPLY, RECOVER)
   ST* y;                        // unknown-face outputs (APPLY, RHS)
   long long trace_stride;
@@ -71,9 +73,12 @@ struct TptArgs {
   CgHook hook;                  // partials == null: no dot
 };
 
-template <int N>
+// Shared memory per pencil slot (elements of T): two buffers of the four
+// staged face arrays (S2+, S2-, S3+, S3-; N rows of R padded entries) and
+// the element's eigenspace solution U (N^2 rows of R).
+template <typename T, int N>
 __host__ __device__ constexpr int tpt_smem_per_pencil() {
-  return 4 * N * N + N * N * N;
+  return 2 * 4 * N * dz_row(N, sizeof(T)) + N * N * dz_row(N, sizeof(T));
 }
 
 template <typename T>
@@ -83,10 +88,16 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// At most 320 threads per CTA (n = 17: 289 threads rounded to warps); three
+// resident CTAs per SM keeps registers at 64 per thread.
 template <typename T, typename ST, int N, int MODE>
-__global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
-  constexpr int N2 = N * N, N3 = N2 * N, NE = (N + 1) / 2;
-  constexpr int PER = tpt_smem_per_pencil<N>();
+__global__ void __launch_bounds__(320, 3) tpt_kernel(const TptArgs<T, ST> a) {
+  constexpr int N2 = N * N, NE = (N + 1) / 2;
+  constexpr int R = dz_row(N, sizeof(T));          // padded row
+  constexpr int VL = Vec<T>::L, NQ = R / VL;
+  constexpr int SF = N * R;                          // one staged face array
+  constexpr int PER = tpt_smem_per_pencil<T, N>();
+  using V = typename Vec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
 
@@ -96,6 +107,8 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
   const int tid = threadIdx.x;
   const int slot = tid / N2;
   const int line = tid - slot * N2;
+  const int lo_i = line % N, hi_i = line / N;     // face node (a, b); x1-line (j, k)
+  const int qpad = lo_i + R * hi_i;                // padded index of the face node
   const long long slot_id = (long long)blockIdx.x * a.ppb + slot;
   const long long pencil = slot_id / a.nseg;
   const int sg = (int)(slot_id - pencil * a.nseg);
@@ -107,99 +120,134 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
   const int e1s = act ? sg * a.seg : 0;
   const int e1e = act ? min(e1s + a.seg, N1e) : 0;
 
-  T* S2p = sm + (act ? slot : 0) * PER;
-  T* S2m = S2p + N2;
-  T* S3p = S2m + N2;
-  T* S3m = S3p + N2;
-  T* U = S3m + N2;
+  T* base = sm + (act ? slot : 0) * PER;
+  T* U = base + 8 * SF;
 
   const long long toff = (long long)rhs * a.trace_stride;
   const ST* xin = (MODE == TPT_RHS) ? nullptr : a.x + toff;
   ST* yout = (MODE == TPT_RECOVER) ? nullptr : a.y + toff;
   const T* gin = (MODE == TPT_APPLY || a.gbd == nullptr) ? nullptr : a.gbd + (long long)rhs * a.bdry_stride;
-  const T* dinv_r = a.dinv + (long long)rhs * a.dinv_rhs_stride;
+  const T* dinv_r = a.dinv ? a.dinv + (long long)rhs * a.dinv_rhs_stride : nullptr;
+  const T lam_r = a.dinv ? T(0) : static_cast<T>(a.lam[rhs]);
 
-  // face-plane strides per direction (faces per plane) and in-plane face index
-  const long long pl0 = (long long)N2e * N3e, pl1 = (long long)N1e * N3e, pl2 = (long long)N1e * N2e;
-  const long long f0 = e2 + (long long)N2e * e3;
-
-  // read one face node: unknown plane -> x, Dirichlet boundary plane -> g-hat
-  auto face_in = [&](int d, int plane, long long fab, long long pl) -> T {
-    if (plane >= m.lo[d] && plane <= m.hi[d]) {
-      if (MODE == TPT_RHS) return T(0);
-      return load_as<ST, T>(xin + (m.blk[d] + (long long)(plane - m.lo[d]) * pl + fab) * N2 + line);
-    }
-    if (gin == nullptr) return T(0);
-    const int side = 2 * d + (plane == 0 ? 0 : 1);
-    return gin[(m.side[side] + fab) * N2 + line];
-  };
+  // Face offsets are 32-bit (trace and boundary sizes per right-hand side
+  // are below 2^31, checked on the host).  An unknown face node has the same
+  // offset in the input x and the output y.
+  const int pl0 = N2e * N3e, pl1 = N1e * N3e, pl2 = N1e * N2e;
+  const int f0 = e2 + N2e * e3;        // x1 faces: (e2, e3)
+  const int f1 = N1e * e3 + e1s;       // x2 faces: (e1, e3) at the segment start
+  const int f2 = N1e * e2 + e1s;       // x3 faces: (e1, e2) at the segment start
   auto unknown = [&](int d, int plane) -> bool { return plane >= m.lo[d] && plane <= m.hi[d]; };
+  // unknown-face offset of direction d on `plane`, or -1
+  auto uoff = [&](int d, int plane, int fab, int pl) -> int {
+    return (act && unknown(d, plane)) ? (int)((m.blk[d] + (long long)(plane - m.lo[d]) * pl + fab) * N2 + line) : -1;
+  };
+  // Dirichlet-face offset (boundary layout) of direction d on `plane`, or -1
+  auto goff = [&](int d, int plane, int fab) -> int {
+    if (MODE == TPT_APPLY || gin == nullptr || !act || unknown(d, plane)) return -1;
+    return (int)((m.side[2 * d + (plane == 0 ? 0 : 1)] + fab) * N2 + line);
+  };
+  int o2l = uoff(1, e2, f1, pl1), o2h = uoff(1, e2 + 1, f1, pl1);
+  int o3l = uoff(2, e3, f2, pl2), o3h = uoff(2, e3 + 1, f2, pl2);
+  int g2l = goff(1, e2, f1), g2h = goff(1, e2 + 1, f1), g3l = goff(2, e3, f2), g3h = goff(2, e3 + 1, f2);
+  auto rd = [&](int o, int g) -> T {
+    if (MODE != TPT_RHS && o >= 0) return load_as<ST, T>(xin + o);
+    if (MODE != TPT_APPLY && g >= 0) return gin[g];
+    return T(0);
+  };
+  auto x1_at = [&](int plane) -> T { return rd(uoff(0, plane, f0, pl0), goff(0, plane, f0)); };
+  auto y1_at = [&](int plane) -> ST* {
+    return yout + (m.blk[0] + (long long)(plane - m.lo[0]) * pl0 + f0) * N2 + line;
+  };
+
+  // values of the first element; the loop prefetches element t+1 while it
+  // computes element t
+  T xlo1 = act ? x1_at(e1s) : T(0);
+  T xhi1 = (act && e1s < e1e) ? x1_at(e1s + 1) : T(0);
+  T x2l = rd(o2l, g2l), x2h = rd(o2h, g2h), x3l = rd(o3l, g3l), x3h = rd(o3h, g3h);
 
   T carry = T(0);
   T dot = T(0);
-  T xlo1 = act ? face_in(0, e1s, f0, pl0) : T(0);
 
   // same trip count in every slot of the CTA (the loop holds barriers)
   for (int t = 0; t < a.seg; ++t) {
     const int e1 = e1s + t;
     const bool live = act && e1 < e1e;
     const long long elem = live ? e1 + (long long)N1e * (e2 + (long long)N2e * e3) : 0;
+    T* S = base + (t & 1) * 4 * SF;   // S2+, S2-, S3+, S3- of this element
+    if (live) {
+      S[qpad] = x2l + x2h;
+      S[SF + qpad] = x2l - x2h;
+      S[2 * SF + qpad] = x3l + x3h;
+      S[3 * SF + qpad] = x3l - x3h;
+    }
+    const T S1 = xlo1 + xhi1, D1 = xlo1 - xhi1;
+    // prefetch element t+1 (in flight during this element's arithmetic)
+    T nx1 = T(0), n2l = T(0), n2h = T(0), n3l = T(0), n3h = T(0);
+    if (live && e1 + 1 < e1e) {
+      auto adv = [](int o) { return o >= 0 ? o + N2 : o; };
+      nx1 = x1_at(e1 + 2);
+      n2l = rd(adv(o2l), adv(g2l)); n2h = rd(adv(o2h), adv(g2h));
+      n3l = rd(adv(o3l), adv(g3l)); n3h = rd(adv(o3h), adv(g3h));
+    }
     const T* mt = a.metric + (m.uniform ? 0 : 4 * elem);
     const T d1 = mt[1], d2 = mt[2], d3 = mt[3];
-    const long long f1 = e1 + (long long)N1e * e3;  // x2-face index in its plane
-    const long long f2 = e1 + (long long)N1e * e2;  // x3-face index in its plane
-    T xhi1 = T(0);
-    if (live) {
-      xhi1 = face_in(0, e1 + 1, f0, pl0);
-      const T x2l = face_in(1, e2, f1, pl1), x2h = face_in(1, e2 + 1, f1, pl1);
-      const T x3l = face_in(2, e3, f2, pl2), x3h = face_in(2, e3 + 1, f2, pl2);
-      S2p[line] = x2l + x2h;
-      S2m[line] = x2l - x2h;
-      S3p[line] = x3l + x3h;
-      S3m[line] = x3l - x3h;
-    }
     __syncthreads();
 
-    // expansion along the x1-line (j, k) = (line % N, line / N), x1 contraction
-    const T S1 = xlo1 + xhi1, D1 = xlo1 - xhi1;
+    // expansion along the x1-line (j, k) = (lo_i, hi_i) and x1 contraction
     T Pp = T(0), Pm = T(0);
     if (live) {
-      const int j = line % N, k = line / N;
+      const int j = lo_i, k = hi_i;
       const T Ap = d1 * S1, Am = d1 * D1;
       const T cjd2 = a.tab.c[j] * d2, ckd3 = a.tab.c[k] * d3;
-      const T* Bs = (j < NE ? S2p : S2m) + N * k;
-      const T* Cs = (k < NE ? S3p : S3m) + N * j;
-      const T* dz = dinv_r + (m.uniform ? 0 : elem * N3) + N * j + N2 * k;
+      const T* Bs = S + (j < NE ? 0 : SF) + R * k;
+      const T* Cs = S + (k < NE ? 2 * SF : 3 * SF) + R * j;
+      const T* dz = dinv_r ? dinv_r + (m.uniform ? 0 : elem * (long long)N2 * R) + R * (j + N * k) : nullptr;
+      const T dzb = dz ? T(0) : fma(d3, a.tab.lam[k], fma(d2, a.tab.lam[j], lam_r * mt[0]));
       const T* sr = (MODE == TPT_APPLY) ? nullptr
-                                         : a.src + (long long)rhs * a.vol_stride + elem * N3 + N * j + N2 * k;
-      T* Ur = U + N * j + N2 * k;
+                                         : a.src + (long long)rhs * a.vol_stride + elem * (long long)(N2 * N) + N * j + N2 * k;
+      T* Ur = U + R * (j + N * k);
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        T F = a.tab.c[i] * (i < NE ? Ap : Am);
-        F = fma(cjd2, Bs[i], F);
-        F = fma(ckd3, Cs[i], F);
-        if (MODE != TPT_APPLY) F -= sr[i];
-        const T u = F * dz[i];
-        Ur[i] = u;
-        if (i < NE) Pp = fma(a.tab.c[i], u, Pp);
-        else Pm = fma(a.tab.c[i], u, Pm);
+      for (int q = 0; q < NQ; ++q) {
+        const V bv = *reinterpret_cast<const V*>(Bs + q * VL);
+        const V cv = *reinterpret_cast<const V*>(Cs + q * VL);
+        V dv;
+        if (dz) dv = *reinterpret_cast<const V*>(dz + q * VL);
+        V uv;
+#pragma unroll
+        for (int l = 0; l < VL; ++l) {
+          const int i = q * VL + l;
+          if (i < N) {
+            T F = a.tab.c[i] * (i < NE ? Ap : Am);
+            F = fma(cjd2, vget(bv, l), F);
+            F = fma(ckd3, vget(cv, l), F);
+            if (MODE != TPT_APPLY) F -= sr[i];
+            const T u = F * (dz ? vget(dv, l) : dz_recip(fma(d1, a.tab.lam[i], dzb)));
+            vset(uv, l, u);
+            if (i < NE) Pp = fma(a.tab.c[i], u, Pp);
+            else Pm = fma(a.tab.c[i], u, Pm);
+          } else {
+            vset(uv, l, T(0));
+          }
+        }
+        *reinterpret_cast<V*>(Ur + q * VL) = uv;
       }
     }
     __syncthreads();
 
     if (live) {
-      const int i = line % N, mm = line / N;
+      const int i = lo_i, mm = hi_i;
       if (MODE == TPT_RECOVER) {
         // w = (f-hat - F_E) / D_Z = -u ; thread (i, mm) writes points (i, mm, k)
-        T* w = a.vout + (long long)rhs * a.vol_stride + elem * N3;
+        T* w = a.vout + (long long)rhs * a.vol_stride + elem * (long long)(N2 * N);
 #pragma unroll
-        for (int k = 0; k < N; ++k) w[i + N * mm + N2 * k] = -U[i + N * mm + N2 * k];
+        for (int k = 0; k < N; ++k) w[i + N * mm + N2 * k] = -U[i + R * (mm + N * k)];
       } else {
         T Qp = T(0), Qm = T(0), Rp = T(0), Rm = T(0);
 #pragma unroll
         for (int mo = 0; mo < N; ++mo) {
-          const T uq = U[i + N * mo + N2 * mm];   // (i, j = mo, k = mm)
-          const T ur = U[i + N * mm + N2 * mo];   // (i, j = mm, k = mo)
+          const T uq = U[i + R * (mo + N * mm)];   // (i, j = mo, k = mm)
+          const T ur = U[i + R * (mm + N * mo)];   // (i, j = mm, k = mo)
           if (mo < NE) { Qp = fma(a.tab.c[mo], uq, Qp); Rp = fma(a.tab.c[mo], ur, Rp); }
           else         { Qm = fma(a.tab.c[mo], uq, Qm); Rm = fma(a.tab.c[mo], ur, Rm); }
         }
@@ -208,25 +256,21 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
         const T two = T(2), half = T(0.5);
         // x2 faces (node (i, k = mm)) on planes e2, e2 + 1
         {
-          const T S = S2p[line], D = S2m[line];
-          const T sum = d2 * (hs * S - two * Qp), dif = d2 * (hd * D - two * Qm);
-          if (unknown(1, e2))
-            red_add(yout + (m.blk[1] + (long long)(e2 - m.lo[1]) * pl1 + f1) * N2 + line, sgn * half * (sum + dif));
-          if (unknown(1, e2 + 1))
-            red_add(yout + (m.blk[1] + (long long)(e2 + 1 - m.lo[1]) * pl1 + f1) * N2 + line, sgn * half * (sum - dif));
-          if (MODE == TPT_APPLY) dot = fma(S, sum, fma(D, dif, dot));
+          const T Sv = S[qpad], Dv = S[SF + qpad];
+          const T sum = d2 * (hs * Sv - two * Qp), dif = d2 * (hd * Dv - two * Qm);
+          if (o2l >= 0) red_add(yout + o2l, sgn * half * (sum + dif));
+          if (o2h >= 0) red_add(yout + o2h, sgn * half * (sum - dif));
+          if (MODE == TPT_APPLY) dot = fma(Sv, sum, fma(Dv, dif, dot));
         }
         // x3 faces (node (i, j = mm)) on planes e3, e3 + 1
         {
-          const T S = S3p[line], D = S3m[line];
-          const T sum = d3 * (hs * S - two * Rp), dif = d3 * (hd * D - two * Rm);
-          if (unknown(2, e3))
-            red_add(yout + (m.blk[2] + (long long)(e3 - m.lo[2]) * pl2 + f2) * N2 + line, sgn * half * (sum + dif));
-          if (unknown(2, e3 + 1))
-            red_add(yout + (m.blk[2] + (long long)(e3 + 1 - m.lo[2]) * pl2 + f2) * N2 + line, sgn * half * (sum - dif));
-          if (MODE == TPT_APPLY) dot = fma(S, sum, fma(D, dif, dot));
+          const T Sv = S[2 * SF + qpad], Dv = S[3 * SF + qpad];
+          const T sum = d3 * (hs * Sv - two * Rp), dif = d3 * (hd * Dv - two * Rm);
+          if (o3l >= 0) red_add(yout + o3l, sgn * half * (sum + dif));
+          if (o3h >= 0) red_add(yout + o3h, sgn * half * (sum - dif));
+          if (MODE == TPT_APPLY) dot = fma(Sv, sum, fma(Dv, dif, dot));
         }
-        // x1 faces (node (j, k) = line): running sum over the pencil
+        // x1 faces (node (j, k) = line): running sum over the segment
         {
           const T sum = d1 * (hs * S1 - two * Pp), dif = d1 * (hd * D1 - two * Pm);
           const T rlo = sgn * half * (sum + dif), rhi = sgn * half * (sum - dif);
@@ -234,22 +278,32 @@ __global__ void __launch_bounds__(512) tpt_kernel(const TptArgs<T, ST> a) {
           // plane e1: inside the segment -> complete sum, store; segment start
           // -> shared with the previous segment (add), unless physical boundary
           if (unknown(0, e1)) {
-            ST* dst = yout + (m.blk[0] + (long long)(e1 - m.lo[0]) * pl0 + f0) * N2 + line;
+            ST* dst = y1_at(e1);
             if (t > 0) store_from<ST, T>(dst, carry + rlo);
             else if (e1 == 0) store_from<ST, T>(dst, rlo);
             else red_add(dst, rlo);
           }
           carry = rhi;
           if (e1 == e1e - 1 && unknown(0, e1e)) {
-            ST* dst = yout + (m.blk[0] + (long long)(e1e - m.lo[0]) * pl0 + f0) * N2 + line;
+            ST* dst = y1_at(e1e);
             if (e1e == N1e) store_from<ST, T>(dst, carry);
             else red_add(dst, carry);
           }
         }
       }
     }
+    // advance the x2/x3 streams by one face (one element along x1)
+    if (o2l >= 0) o2l += N2;
+    if (o2h >= 0) o2h += N2;
+    if (o3l >= 0) o3l += N2;
+    if (o3h >= 0) o3h += N2;
+    if (g2l >= 0) g2l += N2;
+    if (g2h >= 0) g2h += N2;
+    if (g3l >= 0) g3l += N2;
+    if (g3h >= 0) g3h += N2;
     xlo1 = xhi1;
-    __syncthreads();
+    xhi1 = nx1;
+    x2l = n2l; x2h = n2h; x3l = n3l; x3h = n3h;
   }
 
   if (MODE == TPT_APPLY && a.hook.partials != nullptr) {

@@ -10,8 +10,8 @@ template <typename T, typename ST, int N, int MODE>
 cudaError_t tpt_launch_one(const TptArgs<T, ST>& a, int nrhs, cudaStream_t s) {
   if (a.npencils <= 0) return cudaSuccess;
   const int threads = tpt_threads(N, a.ppb);
-  const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<N>() * sizeof(T);
-  if (threads > 512) return cudaErrorInvalidConfiguration;
+  const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<T, N>() * sizeof(T);
+  if (threads > 320) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(tpt_kernel<T, ST, N, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
