@@ -103,8 +103,10 @@ typedef struct {
   int max_iter;            /* total inner CG iterations allowed per right-hand side */
   int max_outer;           /* iterative-refinement steps allowed (>= 1)           */
   hdg_precision inner;     /* precision of the inner CG (FP64, FP32 or BF16)      */
-  double inner_tol;        /* relative residual reduction per inner solve;
-                              <= 0 picks 1e-5 for FP32/BF16 and tol for FP64      */
+  double inner_tol;        /* floor of the relative residual reduction asked of one
+                              inner solve; each inner solve targets
+                              max(floor, tol ||F|| / (2 ||r||)) for the current
+                              outer residual r; <= 0 picks 1e-6 (FP32) or 0 (FP64) */
   int precond;             /* 0: plain CG; 1: face-block Jacobi preconditioner of
                               Sec. 5.1 (Alg. hdg_pc_block), diagonal in the
                               transformed basis (the paper's HDG-trans solver)     */

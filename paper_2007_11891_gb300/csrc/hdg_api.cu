@@ -42,6 +42,7 @@ struct DevBuf {
 
 struct hdg_ctx {
   int device = 0;
+  int sms = 1;            // streaming multiprocessors of the device
   int p = 0, n = 0;
   hdg::Setup1D s1;
   hdg::MeshDev mesh{};
@@ -82,6 +83,8 @@ struct hdg_ctx {
   cudaStream_t cap_stream = nullptr;
   bool capturing = false;
   int graphs_enabled = 1;
+  int loop_graphs_enabled = 1;
+  DevBuf loopctl;   // device loop-trip counter of the CG loop graph
   int seg_override = 0;   // x1 segment length; 0 = automatic
   int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
 };
@@ -201,7 +204,7 @@ hdg_status ensure_dinv(hdg_ctx* c, int nrhs, const double* lam, cudaStream_t s, 
 }
 
 template <typename T, typename ST>
-hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs) {
+hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mode = hdg::TPT_APPLY) {
   hdg::TptArgs<T, ST> a{};
   a.mesh = c->mesh;
   a.tab = tables<T>(c);
@@ -214,11 +217,14 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs) {
   a.vol_stride = c->nvol;
   a.ppb = hdg::tpt_ppb(c->n);
   a.npencils = (long long)c->mesh.ne[1] * c->mesh.ne[2];
-  hdg::tpt_split(c->n, c->mesh.ne, nrhs, &a.seg, &a.nseg);
+  // persistent grid: one resident wave of CTAs, each CTA looping over slot groups
+  const int ctas = c->sms * hdg::tpt_blocks_per_sm<T, ST>(mode, c->n, a.ppb);
+  hdg::tpt_split(c->n, c->mesh.ne, nrhs, ctas, a.ppb, &a.seg, &a.nseg);
   if (c->seg_override > 0) {
     a.seg = std::min(c->seg_override, c->mesh.ne[0]);
     a.nseg = (c->mesh.ne[0] + a.seg - 1) / a.seg;
   }
+  a.max_grid = ctas;
   return a;
 }
 
@@ -272,7 +278,7 @@ hdg_status ensure_reductions(hdg_ctx* c, int nrhs) {
   if (fresh) HDG_CUDA(cudaMemset(c->counters.p, 0, c->counters.bytes));
   HDG_TRY(ensure(c->cgs, sizeof(hdg::CgScalars) * (size_t)nrhs));
   HDG_TRY(ensure(c->flags, sizeof(int) * (size_t)nrhs));
-  HDG_TRY(ensure(c->scal, sizeof(double) * (size_t)nrhs * 4));
+  HDG_TRY(ensure(c->scal, sizeof(double) * (size_t)nrhs * 4));   // rz0, pq, tol, spare
   return HDG_OK;
 }
 
@@ -313,6 +319,22 @@ template <>
 const double* pc_weights<double>(const hdg_ctx* c) { return static_cast<const double*>(c->pc_w64.p); }
 template <>
 const float* pc_weights<float>(const hdg_ctx* c) { return static_cast<const float*>(c->pc_w32.p); }
+
+// Loop control of the device-driven inner CG: after every body trip, keep
+// looping while any right-hand side is still active.  A trip cap derived
+// from the iteration limits bounds the loop independently of the CG flags.
+__global__ void cg_loop_cond(cudaGraphConditionalHandle h, const hdg::CgScalars* cg, const int* flags, int nrhs,
+                             unsigned int* trips, int iters_per_trip) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned int t = ++(*trips);
+  int any = 0, maxit = 0;
+  for (int r = 0; r < nrhs; ++r) {
+    any |= (flags[r] == 0);
+    maxit = max(maxit, cg[r].max_it);
+  }
+  const unsigned int cap = (unsigned int)(maxit / iters_per_trip) + 2u;
+  cudaGraphSetConditional(h, (any && t < cap) ? 1u : 0u);
+}
 
 // `count` CG iterations: operator (fused p^T q), update (alpha, d, r, q = 0,
 // r^T W r, beta), search-direction update.  Three kernels per iteration.
@@ -388,10 +410,91 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
   return true;
 }
 
+// The whole inner CG as one graph launch: a conditional WHILE node whose
+// body runs `kTrip` iterations and then the loop-control kernel.  Returns
+// false (graphs left to the chunked path) where the driver cannot build it.
+constexpr int kTrip = 4;
+template <typename T>
+bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, cudaStream_t s,
+                   hdg_status* st) {
+  *st = HDG_OK;
+  if (!c->loop_graphs_enabled || c->prof_on) return false;
+  if (ensure(c->loopctl, sizeof(unsigned int) * 4) != HDG_OK) return false;
+  std::vector<uintptr_t> key = {0xC0DEu, sizeof(T), (uintptr_t)nrhs, (uintptr_t)dinv, (uintptr_t)lam_buf<T>(c).p,
+                                (uintptr_t)w, (uintptr_t)r, (uintptr_t)d, (uintptr_t)p, (uintptr_t)q,
+                                (uintptr_t)c->flags.p, (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p,
+                                (uintptr_t)c->partials.p, (uintptr_t)c->counters.p, (uintptr_t)c->loopctl.p};
+  GraphEntry* ge = nullptr;
+  for (GraphEntry& g : c->graphs)
+    if (g.key == key) ge = &g;
+  unsigned int* trips = static_cast<unsigned int*>(c->loopctl.p);
+  if (!ge) {
+    auto give_up = [&](cudaGraph_t g) {
+      if (g) cudaGraphDestroy(g);
+      c->loop_graphs_enabled = 0;
+      cudaGetLastError();
+      g_last_error.clear();
+      return false;
+    };
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return give_up(nullptr);
+    cudaGraph_t G = nullptr;
+    if (cudaGraphCreate(&G, 0) != cudaSuccess) return give_up(nullptr);
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, G, 1, cudaGraphCondAssignDefault) != cudaSuccess) return give_up(G);
+    cudaGraphNodeParams mp = {};
+    mp.type = cudaGraphNodeTypeMemset;
+    mp.memset.dst = trips;
+    mp.memset.pitch = 0;
+    mp.memset.value = 0;
+    mp.memset.elementSize = sizeof(unsigned int);
+    mp.memset.width = 1;
+    mp.memset.height = 1;
+    cudaGraphNode_t n1, n2;
+    if (cudaGraphAddNode(&n1, G, nullptr, nullptr, 0, &mp) != cudaSuccess) return give_up(G);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (cudaGraphAddNode(&n2, G, &n1, nullptr, 1, &cp) != cudaSuccess) return give_up(G);
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+        cudaSuccess)
+      return give_up(G);
+    c->capturing = true;
+    hdg_status cs = cg_iterations<T>(c, nrhs, dinv, w, r, d, p, q, kTrip, c->cap_stream);
+    cg_loop_cond<<<1, 32, 0, c->cap_stream>>>(h, static_cast<const hdg::CgScalars*>(c->cgs.p),
+                                             static_cast<const int*>(c->flags.p), nrhs, trips, kTrip);
+    c->capturing = false;
+    cudaGraph_t body_out = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &body_out);
+    cudaGraphExec_t exec = nullptr;
+    if (cs != HDG_OK || e != cudaSuccess || cudaGraphInstantiate(&exec, G, 0) != cudaSuccess) return give_up(G);
+    cudaGraphDestroy(G);
+    c->graphs.push_back(GraphEntry{key, exec});
+    ge = &c->graphs.back();
+  }
+  cudaError_t e = cudaGraphLaunch(ge->exec, s);
+  if (e != cudaSuccess) {
+    *st = fail(HDG_ERR_CUDA, std::string("cudaGraphLaunch (CG loop): ") + cudaGetErrorString(e));
+    return true;
+  }
+  unsigned int ntrip = 0;
+  e = cudaMemcpyAsync(&ntrip, trips, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    *st = fail(HDG_ERR_CUDA, std::string("CG loop: ") + cudaGetErrorString(e));
+    return true;
+  }
+  c->launches += (long long)ntrip * (3LL * kTrip + 1);
+  return true;
+}
+
 // Inner (preconditioned) CG on K-hat d = rhat in precision T for the
 // right-hand sides with active[r] != 0; returns per-rhs iterations and status.
 template <typename T>
-hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat, double tol_inner,
+hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat, const std::vector<double>& tol_r,
                     const std::vector<int>& active, const std::vector<int>& max_it, bool use_pc,
                     std::vector<int>& iters, std::vector<int>& status, cudaStream_t s) {
   const long long T_ = c->ntrace;
@@ -425,14 +528,28 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
     maxit = std::max(maxit, max_it[i]);
   }
   HDG_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
+  // per-rhs relative tolerances (device copy), after the rz0 slot and pq slot
+  double* tol_dev = static_cast<double*>(c->scal.p) + 2 * nrhs;
+  HDG_CUDA(cudaMemcpyAsync(tol_dev, tol_r.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
   // the per-rhs cap is the largest; per-rhs caps below it are enforced on the host afterwards
-  { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_init(cg, flags, rz0, tol_inner, maxit, nrhs, s)); }
+  { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_init(cg, flags, rz0, tol_dev, maxit, nrhs, s)); }
   // p = W r (beta = 0 after init, p = 0)
   { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, w, T_, nrhs, s)); }
   const int chunk = 16;
   std::vector<hdg::CgScalars> hcg(nrhs);
   bool first = true;
-  for (int done_it = 0; done_it < maxit; done_it += chunk) {
+  // first chunk eagerly (sets kernel attributes before any capture), then
+  // the rest of the solve as one device-driven graph launch when possible
+  HDG_TRY(cg_iterations<T>(c, nrhs, dinv, w, r, d, p, q, chunk, s));
+  first = false;
+  {
+    hdg_status gs = HDG_OK;
+    if (cg_loop_graph<T>(c, nrhs, dinv, w, r, d, p, q, s, &gs)) {
+      HDG_TRY(gs);
+      maxit = 0;   // done: skip the chunked loop below
+    }
+  }
+  for (int done_it = chunk; done_it < maxit; done_it += chunk) {
     hdg_status gs = HDG_OK;
     // the first chunk runs eagerly (sets kernel attributes before any capture)
     if (first || !cg_graph<T>(c, nrhs, dinv, w, r, d, p, q, chunk, s, &gs))
@@ -469,7 +586,10 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
   else { o.tol = 1e-10; o.max_iter = 10000; o.max_outer = 20; o.inner = HDG_FP64; o.inner_tol = 0.0; o.precond = 1; }
   if (!(o.tol > 0.0) || o.max_iter < 1 || o.max_outer < 1) return fail(HDG_ERR_INVALID_ARG, "bad solve options");
   if (o.inner == HDG_BF16) return fail(HDG_ERR_UNSUPPORTED, "BF16 inner solve is not available");
-  double tol_inner = o.inner_tol > 0.0 ? o.inner_tol : (o.inner == HDG_FP64 ? 0.1 * o.tol : 1e-5);
+  // each inner solve targets max(floor, tol ||F|| / (2 ||r||)) per rhs: just
+  // enough for the refinement to meet the tolerance, but not below what the
+  // inner precision resolves
+  const double tol_floor = o.inner_tol > 0.0 ? o.inner_tol : (o.inner == HDG_FP64 ? 0.0 : 1e-6);
   for (int r = 0; r < nrhs; ++r)
     if (lam[r] == 0.0 && !c->has_dirichlet)
       return fail(HDG_ERR_SINGULAR, "lambda = 0 without a Dirichlet side: the condensed operator is singular");
@@ -500,7 +620,7 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
     { Timed t_(c, K_FACE, s); HDG_CUDA((hdg::launch_face_transform<double, double>(n, bdry, ghat, c->mesh.nbfaces, nrhs, B, B, c->StM, 1.0, 0, s))); }
   // 3. transformed right-hand side with Dirichlet lift and Neumann load
   {
-    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv, nrhs);
+    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv, nrhs, hdg::TPT_RHS);
     HDG_TRY(zero_for_tpt<double>(c, Fhat, nrhs, a.nseg, s));
     a.y = Fhat;
     a.gbd = ghat;
@@ -553,13 +673,18 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
     }
     if (!any) break;
     std::vector<int> caps(nrhs), it, st;
-    for (int r = 0; r < nrhs; ++r) caps[r] = std::max(0, o.max_iter - total_it[r]);
+    std::vector<double> tol_r(nrhs, 1.0);
+    for (int r = 0; r < nrhs; ++r) {
+      caps[r] = std::max(0, o.max_iter - total_it[r]);
+      const double need = normR2[r] > 0.0 ? 0.5 * o.tol * std::sqrt(normF2[r] / normR2[r]) : 1.0;
+      tol_r[r] = std::min(1.0, std::max(tol_floor, need));
+    }
     // inner solve K-hat d = r-hat; d is left in W_D
     if (o.inner == HDG_FP64) {
-      HDG_TRY(inner_cg<double>(c, nrhs, lam, rhat, tol_inner, active, caps, o.precond != 0, it, st, s));
+      HDG_TRY(inner_cg<double>(c, nrhs, lam, rhat, tol_r, active, caps, o.precond != 0, it, st, s));
       { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_to<double>(xhat, wsp<double>(c, W_D), tot, s)); }
     } else {
-      HDG_TRY(inner_cg<float>(c, nrhs, lam, rhat, tol_inner, active, caps, o.precond != 0, it, st, s));
+      HDG_TRY(inner_cg<float>(c, nrhs, lam, rhat, tol_r, active, caps, o.precond != 0, it, st, s));
       { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_to<float>(xhat, wsp<float>(c, W_D), tot, s)); }
     }
     zero_x = false;
@@ -576,7 +701,7 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
   if (u_out) {
     HDG_TRY(ensure(c->ws[W_WVOL], sizeof(double) * (size_t)V * nrhs));
     double* w = wsp<double>(c, W_WVOL);
-    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv, nrhs);
+    hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv, nrhs, hdg::TPT_RECOVER);
     a.x = xhat;
     a.gbd = ghat;
     a.src = fhat;
@@ -611,6 +736,7 @@ namespace hdg {
 bool ctx_view(const hdg_ctx* c, CtxView* v) {
   if (!c || !v) return false;
   v->device = c->device;
+  v->sms = c->sms;
   v->n = c->n;
   v->uniform = c->uniform;
   v->mesh = c->mesh;
@@ -710,6 +836,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int p, const hdg_options* opts, hdg_c
 
   hdg_ctx* c = new hdg_ctx();
   c->device = dev;
+  c->sms = prop.multiProcessorCount;
   c->p = p;
   c->n = p + 1;
   const char* msg = "";
@@ -831,7 +958,7 @@ void hdg_destroy(hdg_ctx* c) {
     if (b.p) cudaFree(b.p);
   for (auto& v : c->ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
-  for (DevBuf* b : {&c->pc_diag, &c->pc_w64, &c->pc_w32})
+  for (DevBuf* b : {&c->pc_diag, &c->pc_w64, &c->pc_w32, &c->loopctl})
     if (b->p) cudaFree(b->p);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -115,7 +115,9 @@ extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_l
                                                       1.0, 0, s)) != cudaSuccess)
     return cuda_fail(e, "face transform in");
   int seg = 1, nseg = 1;
-  hdg::tpt_split(v.n, v.mesh.ne, nrhs, &seg, &nseg);
+  const int ppb = hdg::tpt_ppb(v.n);
+  const int ctas = v.sms * hdg::tpt_blocks_per_sm<double, double>(hdg::TPT_APPLY, v.n, ppb);
+  hdg::tpt_split(v.n, v.mesh.ne, nrhs, ctas, ppb, &seg, &nseg);
   // the array keeps the previous call's contents: the parts of the operator
   // output that are accumulated with atomics must start at zero (the x2/x3
   // blocks, and everything when x1-pencils are split into segments)
@@ -137,6 +139,7 @@ extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_l
   a.npencils = (long long)v.mesh.ne[1] * v.mesh.ne[2];
   a.seg = seg;
   a.nseg = nseg;
+  a.max_grid = ctas;
   if ((e = hdg::launch_tpt<double, double>(hdg::TPT_APPLY, v.n, a, nrhs, s)) != cudaSuccess)
     return cuda_fail(e, "operator");
   if ((e = hdg::launch_face_transform<double, double>(v.n, yh, d_y, v.mesh.nfaces, nrhs, v.ntrace, v.ntrace, v.MS, 1.0,

@@ -20,7 +20,10 @@ cudaError_t launch_tpt(int mode, int n, TptArgs<T, ST> a, int nrhs, cudaStream_t
 int tpt_ppb(int n);
 int tpt_threads(int n, int ppb);
 long long tpt_blocks(long long nslots, int ppb);
-void tpt_split(int n, const int ne[3], int nrhs, int* seg, int* nseg);
+void tpt_split(int n, const int ne[3], int nrhs, int ctas, int ppb, int* seg, int* nseg);
+// resident CTAs per SM of tpt_kernel<T, ST, n, mode> at ppb slots per CTA
+template <typename T, typename ST>
+int tpt_blocks_per_sm(int mode, int n, int ppb);
 
 // ---- kernels.cu ---------------------------------------------------------------
 // y_f = scale (W (x) W) x_f for every face f (n x n nodes, lower axis fastest),
@@ -77,9 +80,9 @@ struct CgScalars {
   int status;       // 0 ok / converged, 5 not converged, 6 breakdown
 };
 
-// init: rr from dot result, rr_stop = tol^2 rr, done if rr == 0 (or if the
-// right-hand side is already masked in `flags`); flags[r] mirrors done.
-cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, double tol, int max_it,
+// init: rr from dot result, rr_stop = tol[r]^2 rr, done if rr == 0 (or if
+// the right-hand side is already masked in `flags`); flags[r] mirrors done.
+cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, const double* tol, int max_it,
                            int nrhs, cudaStream_t s);
 // alpha = rz / pq; d += alpha p; r -= alpha q; q = 0 (ready for the next
 // operator launch); rz' = r . W r (W = w, or I if w is null); beta = rz'/rz;
@@ -96,6 +99,7 @@ cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w,
 // ---- read-only view of a context's device tables (hdg_api.cu) ----------------
 struct CtxView {
   int device = 0;
+  int sms = 1;
   int n = 0;
   int uniform = 1;
   MeshDev mesh{};

@@ -375,13 +375,13 @@ __global__ void dot_kernel<float>(const float* __restrict__ a, const float* __re
 }
 
 // ---- CG scalars ----------------------------------------------------------------------
-__global__ void cg_init_kernel(CgScalars* cg, int* flags, const double* rr, double tol, int max_it,
+__global__ void cg_init_kernel(CgScalars* cg, int* flags, const double* rr, const double* tol, int max_it,
                                int nrhs) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   CgScalars c;
   c.rr = rr[r];
-  c.rr_stop = tol * tol * c.rr;
+  c.rr_stop = tol[r] * tol[r] * c.rr;
   c.alpha = 0.0;
   c.beta = 0.0;
   c.it = 0;
@@ -647,7 +647,7 @@ cudaError_t launch_pc_invert(const double* diag, double* w64, float* w32, long l
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, double tol, int max_it,
+cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, const double* tol, int max_it,
                            int nrhs, cudaStream_t s) {
   cg_init_kernel<<<(nrhs + 127) / 128, 128, 0, s>>>(cg, flags, rr, tol, max_it, nrhs);
   return cudaGetLastError();

@@ -69,6 +69,7 @@ struct TptArgs {
   long long npencils;           // ne[1] * ne[2]
   int seg;                      // elements per pencil segment (x1 direction)
   int nseg;                     // segments per pencil = ceil(ne[0] / seg)
+  int max_grid;                 // CTAs launched (grid-stride over slot groups); 0 = one per group
   const int* skip;              // per rhs: nonzero -> do nothing (converged), or null
   CgHook hook;                  // partials == null: no dot
 };
@@ -88,10 +89,11 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// At most 320 threads per CTA (n = 17: 289 threads rounded to warps); three
-// resident CTAs per SM keeps registers at 64 per thread.
+// At most 320 threads per CTA (n = 17: 289 threads rounded to warps).  FP32
+// instantiations keep three resident CTAs per SM (64 registers); FP64 ones
+// are bound by the FP64 pipe and get two (up to 96 registers) for ILP.
 template <typename T, typename ST, int N, int MODE>
-__global__ void __launch_bounds__(320, 3) tpt_kernel(const TptArgs<T, ST> a) {
+__global__ void __launch_bounds__(320, sizeof(T) == 4 ? 3 : 2) tpt_kernel(const TptArgs<T, ST> a) {
   constexpr int N2 = N * N, NE = (N + 1) / 2;
   constexpr int R = dz_row(N, sizeof(T));          // padded row
   constexpr int VL = Vec<T>::L, NQ = R / VL;
@@ -109,7 +111,11 @@ __global__ void __launch_bounds__(320, 3) tpt_kernel(const TptArgs<T, ST> a) {
   const int line = tid - slot * N2;
   const int lo_i = line % N, hi_i = line / N;     // face node (a, b); x1-line (j, k)
   const int qpad = lo_i + R * hi_i;                // padded index of the face node
-  const long long slot_id = (long long)blockIdx.x * a.ppb + slot;
+  T dot = T(0);
+  const long long ngroups = (a.npencils * a.nseg + a.ppb - 1) / a.ppb;
+  // persistent grid: each CTA takes slot groups blockIdx.x, + gridDim.x, ...
+  for (long long grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+  const long long slot_id = grp * a.ppb + slot;
   const long long pencil = slot_id / a.nseg;
   const int sg = (int)(slot_id - pencil * a.nseg);
   const bool act = slot < a.ppb && pencil < a.npencils;
@@ -167,7 +173,6 @@ __global__ void __launch_bounds__(320, 3) tpt_kernel(const TptArgs<T, ST> a) {
   T x2l = rd(o2l, g2l), x2h = rd(o2h, g2h), x3l = rd(o3l, g3l), x3h = rd(o3h, g3h);
 
   T carry = T(0);
-  T dot = T(0);
 
   // same trip count in every slot of the CTA (the loop holds barriers)
   for (int t = 0; t < a.seg; ++t) {
@@ -305,12 +310,14 @@ __global__ void __launch_bounds__(320, 3) tpt_kernel(const TptArgs<T, ST> a) {
     xhi1 = nx1;
     x2l = n2l; x2h = n2h; x3l = n3l; x3h = n3h;
   }
+  __syncthreads();   // the next group restages the face buffers
+  }  // slot groups
 
   if (MODE == TPT_APPLY && a.hook.partials != nullptr) {
     // x^T y = sum over element faces of x . r = 1/2 sum (S sum + D dif)
     __shared__ double wsum[16];
     __shared__ bool last;
-    T v = warp_sum(act ? dot : T(0));
+    T v = warp_sum(dot);   // idle threads never added to dot
     if ((tid & 31) == 0) wsum[tid >> 5] = (double)v;
     __syncthreads();
     if (tid == 0) {
