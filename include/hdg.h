@@ -218,6 +218,22 @@ hdg_status hdg_solve_adjoint(hdg_ctx* ctx, int nrhs, const double* h_lambda, con
  * Errors: INVALID_ARG (NULL context, negative length).                    */
 hdg_status hdg_set_x1_segment(hdg_ctx* ctx, int elements);
 
+/* Tuning (not part of the method): number of x1-pencil segments per CTA
+ * (each segment is n^2 threads); 0 restores the automatic choice.  Speed
+ * only.  Errors: INVALID_ARG (NULL context, negative count, or a count whose
+ * CTA would exceed 320 threads).                                          */
+hdg_status hdg_set_slots_per_cta(hdg_ctx* ctx, int slots);
+
+/* Autotuner (not part of the method): times the operator kernel of `prec`
+ * (transformed basis, nrhs right-hand sides with the given lambdas) with
+ * CUDA events on `stream` for every candidate pair of x1-segment length and
+ * slots per CTA, keeps the fastest pair on the context (as the two setters
+ * above would) and returns it with its mean launch time in microseconds.
+ * Allocates workspace (two trace vectors of nrhs x hdg_trace_size()) on
+ * first use; synchronises the stream.  Errors: INVALID_ARG, CUDA, OOM.    */
+hdg_status hdg_autotune(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_precision prec, int* h_best_segment,
+                        int* h_best_slots, double* h_best_us, void* stream);
+
 /* Tuning (not part of the method): where the FP32 operator takes the
  * inverse eigenvalue scaling D_Z^-1 of Sec. 4.1 from.  0 automatic (a table
  * when it fits in L2, else computed in the kernel), 1 always the table,

@@ -16,7 +16,8 @@ BASIS = {"nodal": 0, "transformed": 1}
 
 EXPORTED = ["hdg_setup", "hdg_destroy", "hdg_trace_size", "hdg_volume_size", "hdg_boundary_size",
             "hdg_get_nodes", "hdg_apply", "hdg_apply_static", "hdg_solve", "hdg_solve_adjoint", "hdg_last_error",
-            "hdg_status_string", "hdg_profile", "hdg_profile_read", "hdg_set_x1_segment", "hdg_set_dz_mode"]
+            "hdg_status_string", "hdg_profile", "hdg_profile_read", "hdg_set_x1_segment", "hdg_set_dz_mode",
+            "hdg_set_slots_per_cta", "hdg_autotune"]
 
 
 class HdgMesh(ctypes.Structure):
@@ -80,6 +81,10 @@ def lib():
     L.hdg_solve_adjoint.argtypes = [vp, ci, pd, vp, vp, vp, vp, ctypes.POINTER(HdgSolveOpts),
                                     ctypes.POINTER(HdgSolveInfo), vp]
     L.hdg_solve_adjoint.restype = ci
+    L.hdg_set_slots_per_cta.argtypes = [vp, ci]
+    L.hdg_set_slots_per_cta.restype = ci
+    L.hdg_autotune.argtypes = [vp, ci, pd, ci, ctypes.POINTER(ci), ctypes.POINTER(ci), pd, vp]
+    L.hdg_autotune.restype = ci
     L.hdg_set_dz_mode.argtypes = [vp, ci]
     L.hdg_set_dz_mode.restype = ci
     L.hdg_set_x1_segment.argtypes = [vp, ci]

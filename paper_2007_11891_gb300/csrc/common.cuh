@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace hdg {
 
 constexpr int kMaxNDev = 17;
@@ -20,6 +22,16 @@ struct MeshDev {
   int uniform;        // all elements have the same widths
 };
 
+// Per right-hand-side scalars of the (preconditioned) CG, device resident.
+struct CgScalars {
+  double rr;        // r . z of the current iterate (z = W r)
+  double rr_stop;   // stop when rr <= rr_stop
+  double alpha, beta;
+  int it, max_it;
+  int done;         // 1: stop (converged, iteration cap or breakdown)
+  int status;       // 0 ok / converged, 5 not converged, 6 breakdown
+};
+
 // 1D tables of one degree in the transformed basis (Alg. hdg_op_3d_transformed):
 // c[m] = B_S[m][0] (B_S[m][1] = sigma_m c[m], sigma = +1 for m < n_even),
 // lam[m] = Lambda_m, and H = [[h0, h1], [h1, h0]] = G + C^T M^-1 C.
@@ -29,6 +41,17 @@ struct Tables {
   T lam[kMaxNDev];   // Lambda_m (used when D_Z^-1 is computed in the kernel)
   T h0, h1;
 };
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I = B..E-1, so the
+// body sees its index as a constant expression (constant-bank operands,
+// register-resident arrays, no loop control).
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
 
 // 16-byte vector type per arithmetic type and the padded row length used by
 // the operator's shared-memory arrays and by the D_Z^-1 tables: rows of n

@@ -86,6 +86,7 @@ struct hdg_ctx {
   int loop_graphs_enabled = 1;
   DevBuf loopctl;   // device loop-trip counter of the CG loop graph
   int seg_override = 0;   // x1 segment length; 0 = automatic
+  int ppb_override = 0;   // slots per CTA; 0 = automatic
   int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
 };
 
@@ -93,7 +94,7 @@ namespace {
 
 enum Ws {
   W_XHAT = 0, W_YHAT, W_FHAT_T, W_RHAT, W_TMP, W_FVOL, W_GHAT, W_WVOL,
-  W_R, W_D, W_P, W_Q, W_DOT, W_DOT2
+  W_R, W_D, W_P, W_Q, W_DOT, W_DOT2, W_P2
 };
 
 hdg_status ensure(DevBuf& b, size_t bytes) {
@@ -170,7 +171,10 @@ long long dz_table(const hdg_ctx* c) { return (long long)c->n * c->n * hdg::dz_r
 constexpr size_t kDzTableL2Bytes = 24u << 20;
 template <typename T>
 bool dz_in_kernel(const hdg_ctx* c) {
-  if (sizeof(T) != 4 || c->dz_mode == 1) return false;
+  if (sizeof(T) != 4) return false;
+  // the FP32 kernels index tables with 32-bit offsets
+  if ((size_t)nclass(c) * dz_table<T>(c) >= (size_t(1) << 31)) return true;
+  if (c->dz_mode == 1) return false;
   if (c->dz_mode == 2) return true;
   return !c->uniform && (size_t)nclass(c) * dz_table<T>(c) * sizeof(T) > kDzTableL2Bytes;
 }
@@ -215,7 +219,7 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mod
   a.trace_stride = c->ntrace;
   a.bdry_stride = c->nbdry;
   a.vol_stride = c->nvol;
-  a.ppb = hdg::tpt_ppb(c->n);
+  a.ppb = c->ppb_override > 0 ? c->ppb_override : hdg::tpt_ppb(c->n);
   a.npencils = (long long)c->mesh.ne[1] * c->mesh.ne[2];
   // persistent grid: one resident wave of CTAs, each CTA looping over slot groups
   const int ctas = c->sms * hdg::tpt_blocks_per_sm<T, ST>(mode, c->n, a.ppb);
@@ -336,8 +340,10 @@ __global__ void cg_loop_cond(cudaGraphConditionalHandle h, const hdg::CgScalars*
   cudaGraphSetConditional(h, (any && t < cap) ? 1u : 0u);
 }
 
-// `count` CG iterations: operator (fused p^T q), update (alpha, d, r, q = 0,
-// r^T W r, beta), search-direction update.  Three kernels per iteration.
+// `count` CG iterations (count even).  FP64: operator (fused p^T q), update
+// (alpha, d, r, q = 0, r^T W r, beta), search direction p = W r + beta p.
+// FP32: the search-direction update is fused into the operator's input
+// loads, ping-ponging between p (old, even iterations) and p2: two kernels.
 template <typename T>
 hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, int count,
                          cudaStream_t s) {
@@ -348,11 +354,30 @@ hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, 
   hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), pq};
   const int vb = reduction_blocks(T_);
   for (int k = 0; k < count; ++k) {
-    HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, p, q, s, flags, hook, true)));
-    { Timed t_(c, K_VEC, s);
-      HDG_CUDA(hdg::launch_cg_update<T>(cg, flags, pq, d, r, p, q, w, T_, nrhs, static_cast<double*>(c->partials.p),
-                                        static_cast<unsigned int*>(c->counters.p), vb, s)); }
-    { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, w, T_, nrhs, s)); }
+    if constexpr (sizeof(T) == 4) {
+      T* p2 = wsp<T>(c, W_P2);
+      T* pold = (k & 1) ? p2 : p;
+      T* pnew = (k & 1) ? p : p2;
+      hdg::TptArgs<T, T> a = base_args<T, T>(c, dinv, nrhs);
+      a.x = pold;
+      a.y = q;
+      a.skip = flags;
+      a.hook = hook;
+      a.cg = cg;
+      a.pr = r;
+      a.pw = w;
+      a.pout = pnew;
+      { Timed t(c, K_OP32, s); HDG_CUDA(hdg::launch_tpt<T, T>(hdg::TPT_APPLY, c->n, a, nrhs, s)); }
+      { Timed t_(c, K_VEC, s);
+        HDG_CUDA(hdg::launch_cg_update<T>(cg, flags, pq, d, r, pnew, q, w, T_, nrhs, static_cast<double*>(c->partials.p),
+                                          static_cast<unsigned int*>(c->counters.p), vb, s)); }
+    } else {
+      HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, p, q, s, flags, hook, true)));
+      { Timed t_(c, K_VEC, s);
+        HDG_CUDA(hdg::launch_cg_update<T>(cg, flags, pq, d, r, p, q, w, T_, nrhs, static_cast<double*>(c->partials.p),
+                                          static_cast<unsigned int*>(c->counters.p), vb, s)); }
+      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, w, T_, nrhs, s)); }
+    }
   }
   return HDG_OK;
 }
@@ -366,10 +391,11 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
   *st = HDG_OK;
   if (!c->graphs_enabled || c->prof_on) return false;
   std::vector<uintptr_t> key = {sizeof(T), (uintptr_t)nrhs, (uintptr_t)dinv, (uintptr_t)lam_buf<T>(c).p,
-                                (uintptr_t)w, (uintptr_t)r,
+                                (uintptr_t)c->ws[W_P2].p, (uintptr_t)w, (uintptr_t)r,
                                 (uintptr_t)d, (uintptr_t)p, (uintptr_t)q, (uintptr_t)c->flags.p,
                                 (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p, (uintptr_t)c->partials.p,
-                                (uintptr_t)c->counters.p, (uintptr_t)count};
+                                (uintptr_t)c->counters.p, (uintptr_t)count, (uintptr_t)c->seg_override,
+                                (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode};
   GraphEntry* ge = nullptr;
   for (GraphEntry& g : c->graphs)
     if (g.key == key) ge = &g;
@@ -406,7 +432,7 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
     *st = fail(HDG_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
     return true;
   }
-  c->launches += 3LL * count;
+  c->launches += (sizeof(T) == 4 ? 2LL : 3LL) * count;
   return true;
 }
 
@@ -421,9 +447,11 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
   if (!c->loop_graphs_enabled || c->prof_on) return false;
   if (ensure(c->loopctl, sizeof(unsigned int) * 4) != HDG_OK) return false;
   std::vector<uintptr_t> key = {0xC0DEu, sizeof(T), (uintptr_t)nrhs, (uintptr_t)dinv, (uintptr_t)lam_buf<T>(c).p,
+                                (uintptr_t)c->ws[W_P2].p,
                                 (uintptr_t)w, (uintptr_t)r, (uintptr_t)d, (uintptr_t)p, (uintptr_t)q,
                                 (uintptr_t)c->flags.p, (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p,
-                                (uintptr_t)c->partials.p, (uintptr_t)c->counters.p, (uintptr_t)c->loopctl.p};
+                                (uintptr_t)c->partials.p, (uintptr_t)c->counters.p, (uintptr_t)c->loopctl.p,
+                                (uintptr_t)c->seg_override, (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode};
   GraphEntry* ge = nullptr;
   for (GraphEntry& g : c->graphs)
     if (g.key == key) ge = &g;
@@ -487,7 +515,7 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
     *st = fail(HDG_ERR_CUDA, std::string("CG loop: ") + cudaGetErrorString(e));
     return true;
   }
-  c->launches += (long long)ntrip * (3LL * kTrip + 1);
+  c->launches += (long long)ntrip * ((sizeof(T) == 4 ? 2LL : 3LL) * kTrip + 1);
   return true;
 }
 
@@ -500,6 +528,7 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   const long long T_ = c->ntrace;
   const long long tot = T_ * nrhs;
   for (int i : {W_R, W_D, W_P, W_Q}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
+  if (sizeof(T) == 4) HDG_TRY(ensure(c->ws[W_P2], sizeof(T) * (size_t)tot));
   T* r = wsp<T>(c, W_R);
   T* d = wsp<T>(c, W_D);
   T* p = wsp<T>(c, W_P);
@@ -533,8 +562,8 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   HDG_CUDA(cudaMemcpyAsync(tol_dev, tol_r.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
   // the per-rhs cap is the largest; per-rhs caps below it are enforced on the host afterwards
   { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_init(cg, flags, rz0, tol_dev, maxit, nrhs, s)); }
-  // p = W r (beta = 0 after init, p = 0)
-  { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, w, T_, nrhs, s)); }
+  // p = W r (beta = 0 after init, p = 0); the FP32 operator forms it from p = 0
+  if (sizeof(T) == 8) { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, w, T_, nrhs, s)); }
   const int chunk = 16;
   std::vector<hdg::CgScalars> hcg(nrhs);
   bool first = true;
@@ -760,6 +789,89 @@ const char* hdg_last_error(void) { return g_last_error.c_str(); }
 hdg_status hdg_set_x1_segment(hdg_ctx* c, int elements) {
   if (!c || elements < 0) return fail(HDG_ERR_INVALID_ARG, "NULL context or negative segment length");
   c->seg_override = elements;
+  return HDG_OK;
+}
+
+hdg_status hdg_set_slots_per_cta(hdg_ctx* c, int slots) {
+  if (!c || slots < 0 || hdg::tpt_threads(c->n, slots) > 320)
+    return fail(HDG_ERR_INVALID_ARG, "NULL context or slot count outside 0..(320 threads)");
+  c->ppb_override = slots;
+  return HDG_OK;
+}
+
+hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precision prec, int* h_best_segment,
+                        int* h_best_slots, double* h_best_us, void* stream) {
+  g_last_error.clear();
+  if (!c || nrhs < 1 || prec == HDG_BF16) return fail(HDG_ERR_INVALID_ARG, "NULL context, nrhs < 1 or BF16");
+  HDG_TRY(check_lambda(c, nrhs, h_lambda));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t esz = prec == HDG_FP64 ? 8 : 4;
+  const size_t tot = (size_t)c->ntrace * nrhs;
+  HDG_TRY(ensure(c->ws[W_XHAT], esz * tot));
+  HDG_TRY(ensure(c->ws[W_YHAT], esz * tot));
+  HDG_CUDA(cudaMemsetAsync(c->ws[W_XHAT].p, 0x3c, esz * tot, s));   // finite, non-zero pattern
+  // candidate segment lengths (distinct splits of the x1-pencils) and slots
+  std::vector<int> segs = {0};
+  for (int sg = 1; sg <= c->mesh.ne[0]; ++sg) {
+    const int ns = (c->mesh.ne[0] + sg - 1) / sg;
+    if (sg > 1 && (c->mesh.ne[0] + sg - 2) / (sg - 1) == ns) continue;
+    if (sg <= 4 || sg == c->mesh.ne[0] || (sg & (sg - 1)) == 0) segs.push_back(sg);
+  }
+  std::vector<int> slots = {0};
+  const int base = hdg::tpt_ppb(c->n);
+  for (int pp : {base / 2, base - 1, base + 1, base * 3 / 2})
+    if (pp >= 1 && pp != base && hdg::tpt_threads(c->n, pp) <= 320) slots.push_back(pp);
+  const int keep_seg = c->seg_override, keep_ppb = c->ppb_override;
+  cudaEvent_t e0, e1;
+  HDG_CUDA(cudaEventCreate(&e0));
+  HDG_CUDA(cudaEventCreate(&e1));
+  double best = -1.0;
+  int best_seg = 0, best_ppb = 0;
+  hdg_status st = HDG_OK;
+  for (int pp : slots) {
+    for (int sg : segs) {
+      c->seg_override = sg;
+      c->ppb_override = pp;
+      auto run = [&]() -> hdg_status {
+        if (prec == HDG_FP64) {
+          const double* dinv = nullptr;
+          HDG_TRY(ensure_dinv<double>(c, nrhs, h_lambda, s, &dinv));
+          return tpt_apply<double, double>(c, nrhs, dinv, wsp<double>(c, W_XHAT), wsp<double>(c, W_YHAT), s);
+        }
+        const float* dinv = nullptr;
+        HDG_TRY(ensure_dinv<float>(c, nrhs, h_lambda, s, &dinv));
+        return tpt_apply<float, float>(c, nrhs, dinv, wsp<float>(c, W_XHAT), wsp<float>(c, W_YHAT), s);
+      };
+      for (int w = 0; w < 2 && st == HDG_OK; ++w) st = run();
+      const int reps = 5;
+      if (st == HDG_OK && cudaEventRecord(e0, s) != cudaSuccess) st = fail(HDG_ERR_CUDA, "autotune event");
+      for (int k = 0; k < reps && st == HDG_OK; ++k) st = run();
+      if (st == HDG_OK && cudaEventRecord(e1, s) != cudaSuccess) st = fail(HDG_ERR_CUDA, "autotune event");
+      float ms = 0.f;
+      if (st == HDG_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        st = fail(HDG_ERR_CUDA, "autotune timing");
+      if (st != HDG_OK) break;
+      const double us = 1e3 * ms / reps;
+      if (best < 0.0 || us < best) {
+        best = us;
+        best_seg = sg;
+        best_ppb = pp;
+      }
+    }
+    if (st != HDG_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != HDG_OK) {
+    c->seg_override = keep_seg;
+    c->ppb_override = keep_ppb;
+    return st;
+  }
+  c->seg_override = best_seg;
+  c->ppb_override = best_ppb;
+  if (h_best_segment) *h_best_segment = best_seg;
+  if (h_best_slots) *h_best_slots = best_ppb;
+  if (h_best_us) *h_best_us = best;
   return HDG_OK;
 }
 

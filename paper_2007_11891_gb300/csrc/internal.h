@@ -71,15 +71,6 @@ cudaError_t launch_pc_diag(const MeshDev& m, int n, const Tables<double>& tab, c
 cudaError_t launch_pc_invert(const double* diag, double* w64, float* w32, long long count, cudaStream_t s);
 
 // ---- CG (cg_kernels in kernels.cu) ----------------------------------------------
-struct CgScalars {
-  double rr;        // r . r of the current iterate
-  double rr_stop;   // stop when rr <= rr_stop
-  double alpha, beta;
-  int it, max_it;
-  int done;         // 1: stop (converged, iteration cap or breakdown)
-  int status;       // 0 ok / converged, 5 not converged, 6 breakdown
-};
-
 // init: rr from dot result, rr_stop = tol[r]^2 rr, done if rr == 0 (or if
 // the right-hand side is already masked in `flags`); flags[r] mirrors done.
 cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, const double* tol, int max_it,

@@ -1,15 +1,89 @@
-// FP32 instantiations of the condensed operator.
+// FP32 instantiations of the condensed operator: the specialised apply
+// kernel (tpt_fast.cuh) for the inner CG, the generic kernel otherwise.
+#include "tpt_fast.cuh"
 #include "tpt_launch.cuh"
 
 namespace hdg {
+namespace {
+
+template <int N, bool DZC, bool FUSEP = false>
+int fast_occupancy(int ppb) {
+  static int cached[65] = {0};
+  const int key = ppb < 64 ? ppb : 64;
+  if (cached[key] > 0) return cached[key];
+  const int threads = tpt_threads(N, ppb);
+  const size_t smem = (size_t)ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, FUSEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpt_fast_kernel<N, DZC, FUSEP>, threads, smem) !=
+          cudaSuccess ||
+      nb < 1) {
+    cudaGetLastError();
+    nb = 1;
+  }
+  cached[key] = nb;
+  return nb;
+}
+
+template <int N, bool DZC, bool FUSEP>
+cudaError_t fast_launch(const TptArgs<float, float>& a, int nrhs, cudaStream_t s) {
+  if (a.npencils <= 0) return cudaSuccess;
+  if (a.seg < 1 || a.nseg < 1) return cudaErrorInvalidValue;
+  const int threads = tpt_threads(N, a.ppb);
+  const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
+  if (threads > 320) return cudaErrorInvalidConfiguration;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, FUSEP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  long long blocks = tpt_blocks(a.npencils * a.nseg, a.ppb);
+  if (a.max_grid > 0 && blocks > a.max_grid) blocks = a.max_grid;
+  dim3 grid((unsigned)blocks, (unsigned)nrhs);
+  tpt_fast_kernel<N, DZC, FUSEP><<<grid, threads, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t fast_dispatch_dz(const TptArgs<float, float>& a, int nrhs, cudaStream_t s) {
+  if (a.cg) return a.dinv ? fast_launch<N, false, true>(a, nrhs, s) : fast_launch<N, true, true>(a, nrhs, s);
+  return a.dinv ? fast_launch<N, false, false>(a, nrhs, s) : fast_launch<N, true, false>(a, nrhs, s);
+}
+
+#define FAST_N_SWITCH(n, CALL)                                                  \
+  switch (n) {                                                                  \
+    case 2: return CALL(2); case 3: return CALL(3); case 4: return CALL(4);     \
+    case 5: return CALL(5); case 6: return CALL(6); case 7: return CALL(7);     \
+    case 8: return CALL(8); case 9: return CALL(9); case 10: return CALL(10);   \
+    case 11: return CALL(11); case 12: return CALL(12); case 13: return CALL(13); \
+    case 14: return CALL(14); case 15: return CALL(15); case 16: return CALL(16); \
+    case 17: return CALL(17);                                                   \
+    default: break;                                                             \
+  }
+
+}  // namespace
 
 template <>
 int tpt_blocks_per_sm<float, float>(int mode, int n, int ppb) {
+  if (mode == TPT_APPLY) {
+    // the table and in-kernel variants have the same footprint
+#define OCC(N) fast_occupancy<N, false>(ppb)
+    FAST_N_SWITCH(n, OCC)
+#undef OCC
+    return 1;
+  }
   return tpt_occupancy_dispatch<float, float>(mode, n, ppb);
 }
 
 template <>
 cudaError_t launch_tpt<float, float>(int mode, int n, TptArgs<float, float> a, int nrhs, cudaStream_t s) {
+  if (mode == TPT_APPLY) {
+#define FL(N) fast_dispatch_dz<N>(a, nrhs, s)
+    FAST_N_SWITCH(n, FL)
+#undef FL
+    return cudaErrorInvalidValue;
+  }
   return tpt_dispatch<float, float>(mode, n, a, nrhs, s);
 }
 

@@ -72,6 +72,14 @@ struct TptArgs {
   int max_grid;                 // CTAs launched (grid-stride over slot groups); 0 = one per group
   const int* skip;              // per rhs: nonzero -> do nothing (converged), or null
   CgHook hook;                  // partials == null: no dot
+  // fused search-direction update (FP32 apply only): when cg is set, the
+  // operator input is p_new = W r + beta p_old with p_old = x, r = pr,
+  // W = pw (null: identity), beta = cg[rhs].beta; p_new is written to pout
+  // by exactly one owner slot per face
+  const CgScalars* cg;
+  const ST* pr;
+  const ST* pw;
+  ST* pout;
 };
 
 // Shared memory per pencil slot (elements of T): two buffers of the four

@@ -28,8 +28,8 @@ cudaError_t tpt_launch_one(const TptArgs<T, ST>& a, int nrhs, cudaStream_t s) {
 // resident CTAs per SM of one instantiation (cached per process)
 template <typename T, typename ST, int N, int MODE>
 int tpt_occupancy_one(int ppb) {
-  static int cached[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-  const int key = ppb < 9 ? ppb : 8;
+  static int cached[65] = {0};
+  const int key = ppb < 64 ? ppb : 64;
   if (cached[key] > 0) return cached[key];
   const int threads = tpt_threads(N, ppb);
   const size_t smem = (size_t)ppb * tpt_smem_per_pencil<T, N>() * sizeof(T);

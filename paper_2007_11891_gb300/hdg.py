@@ -5,6 +5,8 @@ dtypes, passes ``data_ptr()`` values and the current torch stream, and
 raises on a non-OK status.
 """
 import ctypes
+import json
+import os
 
 import numpy as np
 import torch
@@ -72,6 +74,36 @@ class HDG:
     def set_x1_segment(self, elements):
         """Operator-kernel tuning: x1-segment length (0 = automatic)."""
         _capi.check(_capi.lib().hdg_set_x1_segment(self._h, int(elements)), "hdg_set_x1_segment")
+
+    def set_slots_per_cta(self, slots):
+        """Operator-kernel tuning: x1-pencil segments per CTA (0 = automatic)."""
+        _capi.check(_capi.lib().hdg_set_slots_per_cta(self._h, int(slots)), "hdg_set_slots_per_cta")
+
+    def autotune(self, precision="fp32", nrhs=1, lam=1.0, cache=None):
+        """Time the operator kernel over its tile candidates (x1-segment
+        length, slots per CTA) and keep the fastest.  With `cache` (a JSON
+        path) results are looked up and stored per GPU, degree, precision,
+        right-hand-side count and mesh.  Returns (segment, slots, us)."""
+        key = "|".join([torch.cuda.get_device_name(), "p%d" % self.p, precision, "nrhs%d" % nrhs,
+                        "ne%dx%dx%d" % self.ne, "bc" + "".join(map(str, self.bc))])
+        table = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+        if key in table:
+            seg, slots, us = table[key]
+            self.set_x1_segment(seg)
+            self.set_slots_per_cta(slots)
+            return seg, slots, us
+        seg, slots, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        st = _capi.lib().hdg_autotune(self._h, nrhs, _lams(lam, nrhs), _capi.PRECISION[precision],
+                                      ctypes.byref(seg), ctypes.byref(slots), ctypes.byref(us), _stream())
+        _capi.check(st, "hdg_autotune")
+        if cache:
+            table[key] = [seg.value, slots.value, us.value]
+            with open(cache, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+        return seg.value, slots.value, us.value
 
     def set_dz_mode(self, mode):
         """FP32 operator tuning: D_Z^-1 from 'auto', 'table' or 'kernel'."""

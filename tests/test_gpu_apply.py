@@ -167,3 +167,20 @@ def test_fp32_dz_table_and_in_kernel_agree(stretched):
     f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 4), device="cuda")
     _, _, info = h.solve(f, lam, tol=1e-10, inner="fp32", return_u=False)
     assert info[0]["status"] == "OK" and info[0]["rel_residual"] <= 1e-10
+
+
+def test_autotune_keeps_results_and_cache(tmp_path):
+    from paper_2007_11891_gb300 import HDG
+    ne, p = (6, 4, 5), 3
+    grid = _grid(ne, False, 2)
+    h = HDG(ne, grid, (0,) * 6, p, 25.0)
+    x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 1), device="cuda", dtype=torch.float32)
+    y0 = h.apply(x, 2.0, basis="transformed")
+    cache = str(tmp_path / "tune.json")
+    seg, slots, us = h.autotune("fp32", 1, 2.0, cache=cache)
+    assert us > 0 and seg >= 0 and slots >= 0
+    assert torch.equal(h.apply(x, 2.0, basis="transformed"), y0)   # tiles never change results
+    h2 = HDG(ne, grid, (0,) * 6, p, 25.0)
+    assert h2.autotune("fp32", 1, 2.0, cache=cache) == (seg, slots, us)   # served from the cache
+    with pytest.raises(Exception):
+        h2.set_slots_per_cta(10000)

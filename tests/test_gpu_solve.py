@@ -170,3 +170,40 @@ def test_unpreconditioned_and_preconditioned_agree(inner):
     assert i1[0]["iterations"] < i0[0]["iterations"]
     for t in (t0, t1):
         assert _oracle_residual(pr, t.cpu().numpy(), f=f) <= 1e-10
+
+
+def test_lumped_mass_option_matches_oracle():
+    # GLL-lumped mass (Sec. 4.1 option): apply and solve against the oracle
+    # built with the same mass matrix
+    from paper_2007_11891_gb300 import HDG
+    ne, p, lam = (3, 4, 2), 4, 1.5
+    grid = _stretched(ne, 31)
+    h = HDG(ne, grid, (0, 1, 0, 0, 0, 0), p, 25.0, mass_lumped=True)
+    pr = Problem(ne, grid, (0, 1, 0, 0, 0, 0), p, 25.0, lam, mass="gll")
+    x = hdg_inputs.uniform_pm1(h.trace_size, 6)
+    y = h.apply(torch.tensor(x, device="cuda"), lam).cpu().numpy()
+    ref = pr.apply(x)
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    f = hdg_inputs.gaussian(h.volume_size, 9)
+    tr, u, info = h.solve(torch.tensor(f, device="cuda"), lam, tol=1e-10, inner="fp32")
+    assert _oracle_residual(pr, tr.cpu().numpy(), f=f) <= 1e-10
+
+
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+def test_poisson_lambda0_inhomogeneous_dirichlet(inner):
+    # the lambda = 0 worst case of Sec. 5.3 with Dirichlet data from a
+    # polynomial: reproduced through the GPU path
+    from paper_2007_11891_gb300 import HDG
+    ne, p = (3, 3, 2), 3
+    grid = _stretched(ne, 41)
+    pr = Problem(ne, grid, (0,) * 6, p, 25.0, 0.0)
+    h = HDG(ne, grid, (0,) * 6, p, 25.0)
+    fld = PolyField(p, np.random.default_rng(41))
+    X = pr.mesh.volume_coords(pr.m1.nodes)
+    f = -fld.lap(X)
+    bd = boundary_data(pr, fld)
+    tol = 1e-12 if inner == "fp64" else 1e-10
+    tr, u, info = h.solve(torch.tensor(f, device="cuda"), 0.0, bdry=torch.tensor(bd, device="cuda"), tol=tol, inner=inner)
+    assert _oracle_residual(pr, tr.cpu().numpy(), f=f, bdry=bd) <= tol
+    scale = np.abs(fld.u(X)).max()
+    assert np.abs(u.cpu().numpy() - fld.u(X)).max() <= (1e-8 if inner == "fp64" else 1e-6) * scale
