@@ -331,8 +331,10 @@ def run_ours(args, rank, world, local_rank):
 def run_sweep(args):
     """One JSON line per measurement: the 32^3 operator sweep (p in
     {2, 4, 8, 12, 16}, FP64 and FP32, transformed basis, L2 flushed per
-    launch) against its roofline, and the 64-rhs batched solve (24^3, p = 7,
-    lambda from {0.1, 1, 100}) mixed vs FP64."""
+    launch) against its roofline, the paper's manufactured solver test
+    (8^3 on (0, 2 pi)^3, lambda = 0, p = 2..16: iterations, error, time per
+    unknown), and the 64-rhs batched solve (24^3, p = 7, lambda from
+    {0.1, 1, 100}) mixed vs FP64."""
     import torch
     from paper_2007_11891_gb300 import HDG
     dev = torch.device("cuda", 0)
@@ -379,6 +381,32 @@ def run_sweep(args):
             print(json.dumps(line), flush=True)
         h.close()
         del x64
+    # the paper's solver test (Sec. 5.3): 8^3 elements on (0, 2 pi)^3, lambda = 0,
+    # inhomogeneous Dirichlet data from u_ex (k = 5), residual reduced by 1e-10
+    cfg = hdg_inputs.WORKLOADS["paper_case"]
+    ne = cfg["ne"]
+    grid = hdg_inputs.grid_lines(ne, length=cfg["length"])
+    for p in range(2, 17):
+        h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
+        X = h.volume_coords()
+        f = torch.tensor(hdg_inputs.paper_case_load(X, cfg["lam"]), device=dev)
+        bd = torch.tensor(hdg_inputs.paper_case_u(h.boundary_coords()[0]), device=dev)
+        uex = hdg_inputs.paper_case_u(X)
+        for inner in ("fp32", "fp64"):
+            run = lambda: h.solve(f, cfg["lam"], bdry=bd, tol=1e-10, inner=inner)
+            run()
+            ms = per_launch_ms(run, 3)
+            _, u, info = run()
+            T = h.trace_size
+            print(json.dumps({"sweep": "paper_case", "workload": "paper_case", "p": p, "inner": inner,
+                              "trace_dofs": T, "ms": ms, "iterations": info[0]["iterations"],
+                              "outer": info[0]["outer"], "rel_residual": info[0]["rel_residual"],
+                              "status": info[0]["status"],
+                              "max_error": float(np.abs(u.cpu().numpy() - uex).max()),
+                              "ns_per_unknown": ms * 1e6 / T,
+                              "ns_per_unknown_iteration": ms * 1e6 / T / max(info[0]["iterations"], 1)}),
+                  flush=True)
+        h.close()
     # batched solve
     cfg = hdg_inputs.WORKLOADS["batched24_p7"]
     ne, p, nrhs = cfg["ne"], cfg["p"], cfg["nrhs"]

@@ -21,6 +21,10 @@ and a manufactured solution, Sec. 4.3 and Sec. 5.3):
 * ``adjoint32_p6``   32^3 uniform, p = 6, lambda = 5, f ~ N(0, 1)
                      (seed 11897), target u_t = sum of 8 sinusoids
                      (seed 11896); finite-difference copy at 4^3, p = 3.
+* ``paper_case``     the paper's own solver test (Sec. 5.3): 8^3 uniform
+                     elements on (0, 2 pi)^3, lambda = 0, tau_hat = 25,
+                     inhomogeneous Dirichlet data and load from the
+                     manufactured solution u_ex with stiffness k = 5.
 """
 
 import numpy as np
@@ -33,11 +37,12 @@ WORKLOADS = {
     "uniform32": dict(ne=(32, 32, 32), p=8, lam=1.0, stretched=False),
     "batched24_p7": dict(ne=(24, 24, 24), p=7, lam=None, stretched=False, nrhs=64),
     "adjoint32_p6": dict(ne=(32, 32, 32), p=6, lam=5.0, stretched=False),
+    "paper_case": dict(ne=(8, 8, 8), p=8, lam=0.0, stretched=False, length=2.0 * np.pi),
 }
 
 
-def grid_lines(ne, stretched=False, seeds=(11892, 11893, 11894)):
-    """Grid-line coordinates per direction on [0, 1]: uniform, or widths
+def grid_lines(ne, stretched=False, seeds=(11892, 11893, 11894), length=1.0):
+    """Grid-line coordinates per direction on [0, length]: uniform, or widths
     drawn uniform in [0.5, 2] with one seed per direction and normalised."""
     out = []
     for d in range(3):
@@ -46,7 +51,7 @@ def grid_lines(ne, stretched=False, seeds=(11892, 11893, 11894)):
         else:
             w = np.ones(ne[d])
         x = np.concatenate([[0.0], np.cumsum(w)])
-        out.append(x / x[-1])
+        out.append(length * x / x[-1])
     return out
 
 
@@ -92,3 +97,53 @@ def smooth_target(X, coeffs):
     a, k, phi = coeffs
     X = np.asarray(X, dtype=np.float64)
     return np.sin(2.0 * np.pi * X @ k.T + phi[None, :]) @ a
+
+
+# ---- manufactured solution of the paper's solver test (Sec. 5.3) ---------------
+# u_ex = cos(k (x1 - 3 x2 + 2 x3)) sin(k (1 + x1)) sin(k (1 - x2))
+#        sin(k (2 x1 + x2)) sin(k (3 x1 - 2 x2 + 2 x3))
+# is a product of factors g_m = trig_m(theta_m), theta_m = k (a_m . x + c_m).
+# With g_m' the derivative of trig_m: grad g_m = k a_m g_m' and
+# laplace g_m = -k^2 |a_m|^2 g_m, so
+# laplace u = -k^2 sum_m |a_m|^2 u + 2 k^2 sum_{m<l} (a_m . a_l) g_m' g_l' prod_{others} g.
+_PAPER_FACTORS = (  # (a_m, c_m, is_cos)
+    ((1.0, -3.0, 2.0), 0.0, True),
+    ((1.0, 0.0, 0.0), 1.0, False),
+    ((0.0, -1.0, 0.0), 1.0, False),
+    ((2.0, 1.0, 0.0), 0.0, False),
+    ((3.0, -2.0, 2.0), 0.0, False),
+)
+
+
+def _paper_case_parts(X, k):
+    X = np.asarray(X, dtype=np.float64)
+    g, dg, a = [], [], []
+    for av, c, is_cos in _PAPER_FACTORS:
+        av = np.asarray(av)
+        th = k * (X @ av + c)
+        g.append(np.cos(th) if is_cos else np.sin(th))
+        dg.append(-np.sin(th) if is_cos else np.cos(th))
+        a.append(av)
+    return g, dg, a
+
+
+def paper_case_u(X, k=5.0):
+    """u_ex at coordinates X (m, 3)."""
+    g, _, _ = _paper_case_parts(X, k)
+    return np.prod(g, axis=0)
+
+
+def paper_case_load(X, lam=0.0, k=5.0):
+    """f = lambda u_ex - laplace u_ex at coordinates X (m, 3)."""
+    g, dg, a = _paper_case_parts(X, k)
+    u = np.prod(g, axis=0)
+    lap = -k * k * sum(a_m @ a_m for a_m in a) * u
+    nf = len(g)
+    for m in range(nf):
+        for l in range(m + 1, nf):
+            rest = np.ones_like(u)
+            for o in range(nf):
+                if o != m and o != l:
+                    rest = rest * g[o]
+            lap = lap + 2.0 * k * k * (a[m] @ a[l]) * dg[m] * dg[l] * rest
+    return lam * u - lap

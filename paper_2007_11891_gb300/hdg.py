@@ -131,6 +131,44 @@ class HDG:
         _capi.check(_capi.lib().hdg_get_nodes(self._h, out), "hdg_get_nodes")
         return np.array(out[:])
 
+    # -- node coordinates of the data layouts (host-side bookkeeping) ----------
+    def _lines(self, nodes):
+        # per direction: (ne[d], n) physical node coordinates of each element
+        g = [np.asarray(self._grid[d][:], dtype=np.float64) for d in range(3)]
+        return [g[d][:-1, None] + (nodes[None, :] + 1.0) * 0.5 * np.diff(g[d])[:, None] for d in range(3)], g
+
+    def volume_coords(self):
+        """(volume_size, 3) coordinates of the volume nodes in the volume layout
+        (element e1 + N1 (e2 + N2 e3), node i + n j + n^2 k)."""
+        x, _ = self._lines(self.nodes())
+        n, (N1, N2, N3) = self.n, self.ne
+        X = np.empty((N3, N2, N1, n, n, n, 3))
+        X[..., 0] = x[0][None, None, :, None, None, :]
+        X[..., 1] = x[1][None, :, None, None, :, None]
+        X[..., 2] = x[2][:, None, None, :, None, None]
+        return X.reshape(-1, 3)
+
+    def boundary_coords(self):
+        """(boundary_size, 3) coordinates of the boundary-data nodes and the
+        (boundary_size, 3) outer unit normals, in the boundary layout (sides
+        x1-, x1+, x2-, x2+, x3-, x3+; faces a + Na b; nodes lower axis fastest)."""
+        x, g = self._lines(self.nodes())
+        n = self.n
+        P, Nrm = [], []
+        for side in range(6):
+            d, s = divmod(side, 2)
+            a, b = [ax for ax in range(3) if ax != d]
+            na, nb = self.ne[a], self.ne[b]
+            F = np.empty((nb, na, n, n, 3))
+            F[..., d] = g[d][-1] if s else g[d][0]
+            F[..., a] = x[a][None, :, None, :]
+            F[..., b] = x[b][:, None, :, None]
+            P.append(F.reshape(-1, 3))
+            nrm = np.zeros((nb * na * n * n, 3))
+            nrm[:, d] = 1.0 if s else -1.0
+            Nrm.append(nrm)
+        return np.concatenate(P), np.concatenate(Nrm)
+
     # -- operator ------------------------------------------------------------
     def apply(self, x, lam, basis="nodal", out=None):
         """y = K x (homogeneous Dirichlet data).  x: (T,) or (nrhs, T) CUDA

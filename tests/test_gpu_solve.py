@@ -207,3 +207,38 @@ def test_poisson_lambda0_inhomogeneous_dirichlet(inner):
     assert _oracle_residual(pr, tr.cpu().numpy(), f=f, bdry=bd) <= tol
     scale = np.abs(fld.u(X)).max()
     assert np.abs(u.cpu().numpy() - fld.u(X)).max() <= (1e-8 if inner == "fp64" else 1e-6) * scale
+
+
+def test_layout_coordinates_match_oracle():
+    from paper_2007_11891_gb300 import HDG
+    ne, p = (3, 2, 4), 3
+    grid = _stretched(ne, 7)
+    pr = Problem(ne, grid, (0, 1, 0, 0, 1, 0), p, 25.0, 1.0)
+    h = HDG(ne, grid, (0, 1, 0, 0, 1, 0), p, 25.0)
+    assert np.abs(h.volume_coords() - pr.mesh.volume_coords(pr.m1.nodes)).max() <= 1e-14 * grid[0][-1]
+    X, N = h.boundary_coords()
+    Xo, No = pr.mesh.bdry_coords(pr.m1.nodes)
+    assert np.abs(X - Xo).max() <= 1e-13 and np.array_equal(N, No)
+
+
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+def test_paper_manufactured_case_small(inner):
+    # the solver test of Sec. 5.3 (u_ex with k = 5 on (0, 2 pi)^3, lambda = 0,
+    # inhomogeneous Dirichlet data) on 3^3 elements: the solve meets its
+    # residual in the oracle's own K and F, and the error falls with p
+    from paper_2007_11891_gb300 import HDG
+    ne = (3, 3, 3)
+    grid = hdg_inputs.grid_lines(ne, length=2.0 * np.pi)
+    errs = []
+    for p in (4, 6):
+        h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
+        X = h.volume_coords()
+        f = hdg_inputs.paper_case_load(X)
+        bd = hdg_inputs.paper_case_u(h.boundary_coords()[0])
+        tr, u, info = h.solve(torch.tensor(f, device="cuda"), 0.0, bdry=torch.tensor(bd, device="cuda"),
+                              tol=1e-10, inner=inner)
+        assert info[0]["status"] == "OK"
+        pr = Problem(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT, 0.0)
+        assert _oracle_residual(pr, tr.cpu().numpy(), f=f, bdry=bd) <= 1e-10
+        errs.append(np.abs(u.cpu().numpy() - hdg_inputs.paper_case_u(X)).max())
+    assert errs[1] < 0.5 * errs[0]
