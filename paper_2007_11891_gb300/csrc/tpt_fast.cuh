@@ -25,11 +25,18 @@ namespace hdg {
 #ifndef HDG_FAST_MIN_CTAS
 #define HDG_FAST_MIN_CTAS 2
 #endif
+#ifndef HDG_FUSED_MIN_CTAS
+#define HDG_FUSED_MIN_CTAS 3
+#endif
 
+// Resident CTAs guaranteed per SM.  Plain apply: two (up to 96 registers);
+// a cap of 64 made the compiler rematerialise values (29% more
+// instructions, measured).  Fused search-direction update: three, whose
+// three input streams per face need the extra warps to cover their latency
+// (two CTAs: 34% slower inside the CG loop, measured).
 template <int N, bool DZC, bool FUSEP>
-// Two resident CTAs guaranteed (up to 96 registers): capping at 64 made the
-// compiler rematerialise values and cost 29% more instructions (measured)
-__global__ void __launch_bounds__(320, HDG_FAST_MIN_CTAS) tpt_fast_kernel(const TptArgs<float, float> a) {
+__global__ void __launch_bounds__(320, FUSEP ? HDG_FUSED_MIN_CTAS : HDG_FAST_MIN_CTAS)
+    tpt_fast_kernel(const TptArgs<float, float> a) {
   constexpr int N2 = N * N, NE = (N + 1) / 2;
   constexpr int R = dz_row(N, sizeof(float));
   constexpr int NQ = R / 4;
