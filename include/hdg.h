@@ -210,18 +210,22 @@ hdg_status hdg_solve_adjoint(hdg_ctx* ctx, int nrhs, const double* h_lambda, con
                              const double* d_grad_u, double* d_grad_f, double* d_grad_lambda,
                              const hdg_solve_opts* opts, hdg_solve_info* h_info, void* stream);
 
-/* Tuning (not part of the method): the length, in elements, of the x1-pencil
- * segments that one CTA slot of the operator kernel marches over (faces
- * inside a segment are summed in registers, faces on segment ends with two
- * atomic adds).  0 restores the automatic choice (enough segments to fill
- * the GPU).  Speed only: every value gives bitwise identical results.
- * Errors: INVALID_ARG (NULL context, negative length).                    */
+/* Tuning (not part of the method): the number of elements one CTA slot of
+ * the operator kernel marches over along x1.  FP64 kernels: a segment of
+ * one x1-pencil; FP32 apply kernel: a contiguous run in element order that
+ * may continue into the next pencil.  The x1-face between consecutive
+ * elements of a slot is summed in registers, other shared faces with two
+ * atomic adds onto zero.  0 restores the automatic choice (one resident
+ * wave of slots covers the mesh).  Speed only: every value gives bitwise
+ * identical results.  Errors: INVALID_ARG (NULL context, negative length). */
 hdg_status hdg_set_x1_segment(hdg_ctx* ctx, int elements);
 
-/* Tuning (not part of the method): number of x1-pencil segments per CTA
- * (each segment is n^2 threads); 0 restores the automatic choice.  Speed
- * only.  Errors: INVALID_ARG (NULL context, negative count, or a count whose
- * CTA would exceed 320 threads).                                          */
+/* Tuning (not part of the method): number of element slots per CTA of the
+ * operator kernels (each slot is n^2 threads); 0 restores the automatic
+ * choice.  Speed only.  Errors: INVALID_ARG (NULL context, negative count,
+ * or a count whose CTA would exceed 320 threads); an FP32 apply whose CTA
+ * would exceed 256 threads (n <= 16) fails with CUDA (invalid
+ * configuration).                                                          */
 hdg_status hdg_set_slots_per_cta(hdg_ctx* ctx, int slots);
 
 /* Autotuner (not part of the method): times the operator kernel of `prec`

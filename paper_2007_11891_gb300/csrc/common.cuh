@@ -24,9 +24,10 @@ struct MeshDev {
 
 // Per right-hand-side scalars of the (preconditioned) CG, device resident.
 struct CgScalars {
-  double rr;        // r . z of the current iterate (z = W r)
+  double rr;        // gamma = r . u of the current iterate (u = W r)
+  double rr_old;    // gamma of the previous iterate
   double rr_stop;   // stop when rr <= rr_stop
-  double alpha, beta;
+  double alpha, beta;   // of the last step
   int it, max_it;
   int done;         // 1: stop (converged, iteration cap or breakdown)
   int status;       // 0 ok / converged, 5 not converged, 6 breakdown

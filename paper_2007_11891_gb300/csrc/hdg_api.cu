@@ -94,7 +94,7 @@ namespace {
 
 enum Ws {
   W_XHAT = 0, W_YHAT, W_FHAT_T, W_RHAT, W_TMP, W_FVOL, W_GHAT, W_WVOL,
-  W_R, W_D, W_P, W_Q, W_DOT, W_DOT2, W_P2
+  W_R, W_D, W_P, W_Q, W_DOT, W_DOT2, W_U, W_S
 };
 
 hdg_status ensure(DevBuf& b, size_t bytes) {
@@ -229,6 +229,11 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mod
     a.nseg = (c->mesh.ne[0] + a.seg - 1) / a.seg;
   }
   a.max_grid = ctas;
+  // FP32 apply: equal contiguous runs, one per slot of a resident wave (per
+  // right-hand side: the wave is shared by the batch)
+  const long long nelem = (long long)c->nelem * std::max(nrhs, 1);
+  const long long slots = std::max(1LL, (long long)ctas * a.ppb);
+  a.chunk = c->seg_override > 0 ? c->seg_override : (int)std::max(1LL, (nelem + slots - 1) / slots);
   return a;
 }
 
@@ -248,7 +253,8 @@ template <typename T, typename ST>
 hdg_status tpt_apply(hdg_ctx* c, int nrhs, const T* dinv, const ST* x, ST* y, cudaStream_t s,
                      const int* skip = nullptr, hdg::CgHook hook = hdg::CgHook{}, bool zeroed = false) {
   hdg::TptArgs<T, ST> a = base_args<T, ST>(c, dinv, nrhs);
-  if (!zeroed) HDG_TRY(zero_for_tpt<ST>(c, y, nrhs, a.nseg, s));
+  // the FP32 kernel's runs may split any x1-pencil: zero the whole output
+  if (!zeroed) HDG_TRY(zero_for_tpt<ST>(c, y, nrhs, sizeof(T) == 4 ? 2 : a.nseg, s));
   a.x = x;
   a.y = y;
   a.skip = skip;
@@ -340,44 +346,26 @@ __global__ void cg_loop_cond(cudaGraphConditionalHandle h, const hdg::CgScalars*
   cudaGraphSetConditional(h, (any && t < cap) ? 1u : 0u);
 }
 
-// `count` CG iterations (count even).  FP64: operator (fused p^T q), update
-// (alpha, d, r, q = 0, r^T W r, beta), search direction p = W r + beta p.
-// FP32: the search-direction update is fused into the operator's input
-// loads, ping-ponging between p (old, even iterations) and p2: two kernels.
+// `count` CG iterations, two kernels each: the operator w = K-hat u with the
+// fused u^T w, then the single-reduction CG step (launch_cg_step).  Vectors:
+// x (d), r, u = W r, w (q), p, s = K-hat p.
 template <typename T>
 hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, int count,
                          cudaStream_t s) {
   const long long T_ = c->ntrace;
   int* flags = static_cast<int*>(c->flags.p);
   hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
-  double* pq = static_cast<double*>(c->scal.p) + nrhs;
-  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), pq};
+  double* uw = static_cast<double*>(c->scal.p) + nrhs;
+  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), uw};
+  T* u = wsp<T>(c, W_U);
+  T* sv = wsp<T>(c, W_S);
   const int vb = reduction_blocks(T_);
   for (int k = 0; k < count; ++k) {
-    if constexpr (sizeof(T) == 4) {
-      T* p2 = wsp<T>(c, W_P2);
-      T* pold = (k & 1) ? p2 : p;
-      T* pnew = (k & 1) ? p : p2;
-      hdg::TptArgs<T, T> a = base_args<T, T>(c, dinv, nrhs);
-      a.x = pold;
-      a.y = q;
-      a.skip = flags;
-      a.hook = hook;
-      a.cg = cg;
-      a.pr = r;
-      a.pw = w;
-      a.pout = pnew;
-      { Timed t(c, K_OP32, s); HDG_CUDA(hdg::launch_tpt<T, T>(hdg::TPT_APPLY, c->n, a, nrhs, s)); }
-      { Timed t_(c, K_VEC, s);
-        HDG_CUDA(hdg::launch_cg_update<T>(cg, flags, pq, d, r, pnew, q, w, T_, nrhs, static_cast<double*>(c->partials.p),
-                                          static_cast<unsigned int*>(c->counters.p), vb, s)); }
-    } else {
-      HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, p, q, s, flags, hook, true)));
-      { Timed t_(c, K_VEC, s);
-        HDG_CUDA(hdg::launch_cg_update<T>(cg, flags, pq, d, r, p, q, w, T_, nrhs, static_cast<double*>(c->partials.p),
-                                          static_cast<unsigned int*>(c->counters.p), vb, s)); }
-      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, w, T_, nrhs, s)); }
-    }
+    HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, u, q, s, flags, hook, true)));
+    Timed t_(c, K_VEC, s);
+    HDG_CUDA(hdg::launch_cg_step<T>(cg, flags, uw, d, r, u, q, p, sv, w, T_, nrhs,
+                                    static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p),
+                                    vb, s));
   }
   return HDG_OK;
 }
@@ -391,7 +379,7 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
   *st = HDG_OK;
   if (!c->graphs_enabled || c->prof_on) return false;
   std::vector<uintptr_t> key = {sizeof(T), (uintptr_t)nrhs, (uintptr_t)dinv, (uintptr_t)lam_buf<T>(c).p,
-                                (uintptr_t)c->ws[W_P2].p, (uintptr_t)w, (uintptr_t)r,
+                                (uintptr_t)c->ws[W_U].p, (uintptr_t)c->ws[W_S].p, (uintptr_t)w, (uintptr_t)r,
                                 (uintptr_t)d, (uintptr_t)p, (uintptr_t)q, (uintptr_t)c->flags.p,
                                 (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p, (uintptr_t)c->partials.p,
                                 (uintptr_t)c->counters.p, (uintptr_t)count, (uintptr_t)c->seg_override,
@@ -432,7 +420,7 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
     *st = fail(HDG_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
     return true;
   }
-  c->launches += (sizeof(T) == 4 ? 2LL : 3LL) * count;
+  c->launches += 2LL * count;
   return true;
 }
 
@@ -447,7 +435,7 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
   if (!c->loop_graphs_enabled || c->prof_on) return false;
   if (ensure(c->loopctl, sizeof(unsigned int) * 4) != HDG_OK) return false;
   std::vector<uintptr_t> key = {0xC0DEu, sizeof(T), (uintptr_t)nrhs, (uintptr_t)dinv, (uintptr_t)lam_buf<T>(c).p,
-                                (uintptr_t)c->ws[W_P2].p,
+                                (uintptr_t)c->ws[W_U].p, (uintptr_t)c->ws[W_S].p,
                                 (uintptr_t)w, (uintptr_t)r, (uintptr_t)d, (uintptr_t)p, (uintptr_t)q,
                                 (uintptr_t)c->flags.p, (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p,
                                 (uintptr_t)c->partials.p, (uintptr_t)c->counters.p, (uintptr_t)c->loopctl.p,
@@ -515,7 +503,7 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
     *st = fail(HDG_ERR_CUDA, std::string("CG loop: ") + cudaGetErrorString(e));
     return true;
   }
-  c->launches += (long long)ntrip * ((sizeof(T) == 4 ? 2LL : 3LL) * kTrip + 1);
+  c->launches += (long long)ntrip * (2LL * kTrip + 1);
   return true;
 }
 
@@ -527,12 +515,12 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
                     std::vector<int>& iters, std::vector<int>& status, cudaStream_t s) {
   const long long T_ = c->ntrace;
   const long long tot = T_ * nrhs;
-  for (int i : {W_R, W_D, W_P, W_Q}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
-  if (sizeof(T) == 4) HDG_TRY(ensure(c->ws[W_P2], sizeof(T) * (size_t)tot));
+  for (int i : {W_R, W_D, W_P, W_Q, W_U, W_S}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
   T* r = wsp<T>(c, W_R);
   T* d = wsp<T>(c, W_D);
   T* p = wsp<T>(c, W_P);
   T* q = wsp<T>(c, W_Q);
+  T* u = wsp<T>(c, W_U);
   const T* dinv = nullptr;
   HDG_TRY(ensure_dinv<T>(c, nrhs, lam, s, &dinv));
   const T* w = nullptr;
@@ -546,9 +534,7 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
 
   if (sizeof(T) == 8) HDG_CUDA(cudaMemcpyAsync(r, rhat, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
   else { Timed t_(c, K_VEC, s); HDG_CUDA((hdg::launch_convert<double, float>(rhat, reinterpret_cast<float*>(r), tot, s))); }
-  HDG_CUDA(cudaMemsetAsync(d, 0, sizeof(T) * tot, s));
-  HDG_CUDA(cudaMemsetAsync(p, 0, sizeof(T) * tot, s));
-  HDG_CUDA(cudaMemsetAsync(q, 0, sizeof(T) * tot, s));
+  for (T* v : {d, p, q, u, wsp<T>(c, W_S)}) HDG_CUDA(cudaMemsetAsync(v, 0, sizeof(T) * tot, s));
   HDG_TRY(dot<T>(c, r, r, T_, nrhs, rz0, s, w));
   std::vector<int> hflags(nrhs);
   int maxit = 0;
@@ -557,13 +543,13 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
     maxit = std::max(maxit, max_it[i]);
   }
   HDG_CUDA(cudaMemcpyAsync(flags, hflags.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s));
-  // per-rhs relative tolerances (device copy), after the rz0 slot and pq slot
+  // per-rhs relative tolerances (device copy), after the rz0 slot and u^T w slot
   double* tol_dev = static_cast<double*>(c->scal.p) + 2 * nrhs;
   HDG_CUDA(cudaMemcpyAsync(tol_dev, tol_r.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
   // the per-rhs cap is the largest; per-rhs caps below it are enforced on the host afterwards
   { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_init(cg, flags, rz0, tol_dev, maxit, nrhs, s)); }
-  // p = W r (beta = 0 after init, p = 0); the FP32 operator forms it from p = 0
-  if (sizeof(T) == 8) { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, p, r, w, T_, nrhs, s)); }
+  // u_0 = W r_0 (beta = 0 after init, u = 0)
+  { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, u, r, w, T_, nrhs, s)); }
   const int chunk = 16;
   std::vector<hdg::CgScalars> hcg(nrhs);
   bool first = true;
@@ -819,8 +805,9 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
   }
   std::vector<int> slots = {0};
   const int base = hdg::tpt_ppb(c->n);
+  const int max_threads = prec == HDG_FP64 ? 320 : hdg::fast_max_threads(c->n);
   for (int pp : {base / 2, base - 1, base + 1, base * 3 / 2})
-    if (pp >= 1 && pp != base && hdg::tpt_threads(c->n, pp) <= 320) slots.push_back(pp);
+    if (pp >= 1 && pp != base && hdg::tpt_threads(c->n, pp) <= max_threads) slots.push_back(pp);
   const int keep_seg = c->seg_override, keep_ppb = c->ppb_override;
   cudaEvent_t e0, e1;
   HDG_CUDA(cudaEventCreate(&e0));

@@ -75,13 +75,14 @@ cudaError_t launch_pc_invert(const double* diag, double* w64, float* w32, long l
 // the right-hand side is already masked in `flags`); flags[r] mirrors done.
 cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, const double* tol, int max_it,
                            int nrhs, cudaStream_t s);
-// alpha = rz / pq; d += alpha p; r -= alpha q; q = 0 (ready for the next
-// operator launch); rz' = r . W r (W = w, or I if w is null); beta = rz'/rz;
-// the last block updates the scalars and flags[r] (no effect once done)
+// One step of the single-reduction CG (Chronopoulos-Gear) after the operator
+// launch w = K u with its fused u . w in uw[r]: updates p, s, x, r, u = W r
+// (W = I if null), zeroes w, and the last block stores gamma = r . u, the
+// step scalars and flags[r] (no effect once done).
 template <typename T>
-cudaError_t launch_cg_update(CgScalars* cg, int* flags, const double* pq, T* d, T* r, const T* p,
-                             T* q, const T* w, long long len, int nrhs, double* partials,
-                             unsigned int* counter, int blocks, cudaStream_t s);
+cudaError_t launch_cg_step(CgScalars* cg, int* flags, const double* uw, T* x, T* r, T* u, T* w, T* p, T* sv,
+                           const T* W, long long len, int nrhs, double* partials, unsigned int* counter,
+                           int blocks, cudaStream_t s);
 // p = W r + beta p (skips finished right-hand sides)
 template <typename T>
 cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w, long long len, int nrhs,

@@ -83,7 +83,62 @@ __global__ void face_transform_kernel(const TI* __restrict__ x, TO* __restrict__
 }
 
 // ---- volume transforms: y_e = s_e (A (x) A (x) A) x_e -------------------------
-template <int N>
+// One 1D line transform out[a] = sum_i A[a][i] in[i] of n values.
+// PAR = 0: dense, n^2 multiply-adds.  The basis-change matrices inherit the
+// mirror symmetry of the GLL points, with the eigenmodes ordered [even | odd]
+// (m < NE even, sigma_m = +1; else odd, sigma_m = -1):
+// PAR = 1 (rows are modes: S^T, S^T M): A[m][n-1-i] = sigma_m A[m][i], so an
+//   even mode only sees in[i] + in[n-1-i] and an odd one in[i] - in[n-1-i];
+// PAR = 2 (columns are modes: S, M S): A[n-1-i][m] = sigma_m A[i][m], so
+//   out[i] = E_i + O_i and out[n-1-i] = E_i - O_i with the even- and
+//   odd-mode partial sums E_i, O_i.
+// Either parity form takes about n^2 / 2 multiply-adds.
+template <int N, int PAR>
+__device__ __forceinline__ void line_transform(const Mat1D<double>& A, const double (&in)[N], double (&out)[N]) {
+  constexpr int NE = (N + 1) / 2, H = N / 2;
+  if constexpr (PAR == 1) {
+    double sp[NE], dm[H > 0 ? H : 1];
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+      sp[i] = in[i] + in[N - 1 - i];
+      dm[i] = in[i] - in[N - 1 - i];
+    }
+    if constexpr (N % 2 == 1) sp[H] = in[H];
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      double v = 0.0;
+      if (a < NE) {
+#pragma unroll
+        for (int i = 0; i < NE; ++i) v = fma(A.a[a * N + i], sp[i], v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < H; ++i) v = fma(A.a[a * N + i], dm[i], v);
+      }
+      out[a] = v;
+    }
+  } else if constexpr (PAR == 2) {
+#pragma unroll
+    for (int i = 0; i < NE; ++i) {
+      double ev = 0.0, od = 0.0;
+#pragma unroll
+      for (int m = 0; m < NE; ++m) ev = fma(A.a[i * N + m], in[m], ev);
+#pragma unroll
+      for (int m = NE; m < N; ++m) od = fma(A.a[i * N + m], in[m], od);
+      out[i] = ev + od;
+      if (N - 1 - i != i) out[N - 1 - i] = ev - od;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      double v = 0.0;
+#pragma unroll
+      for (int i = 0; i < N; ++i) v = fma(A.a[a * N + i], in[i], v);
+      out[a] = v;
+    }
+  }
+}
+
+template <int N, int PAR>
 __global__ void volume_transform_kernel(const double* __restrict__ x, double* __restrict__ y,
                                         long long nelem, long long stride, const Mat1D<double> A,
                                         const double* __restrict__ metric, int uniform, int use_d0,
@@ -107,46 +162,34 @@ __global__ void volume_transform_kernel(const double* __restrict__ x, double* __
   __syncthreads();
   // pass 1 (x1): B1[k][j][a] = sum_i A[a][i] B0[k][j][i]; thread (j, k) = (lo, hi)
   if (act) {
-    double in[N];
+    double in[N], out[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) in[i] = B0[i + N * lo + N2 * hi];
+    line_transform<N, PAR>(A, in, out);
 #pragma unroll
-    for (int aa = 0; aa < N; ++aa) {
-      double v = 0.0;
-#pragma unroll
-      for (int i = 0; i < N; ++i) v = fma(A.a[aa * N + i], in[i], v);
-      B1[aa + N * lo + N2 * hi] = v;
-    }
+    for (int aa = 0; aa < N; ++aa) B1[aa + N * lo + N2 * hi] = out[aa];
   }
   __syncthreads();
   // pass 2 (x2): B0[k][b][i] = sum_j A[b][j] B1[k][j][i]; thread (i, k) = (lo, hi)
   if (act) {
-    double in[N];
+    double in[N], out[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) in[j] = B1[lo + N * j + N2 * hi];
+    line_transform<N, PAR>(A, in, out);
 #pragma unroll
-    for (int bb = 0; bb < N; ++bb) {
-      double v = 0.0;
-#pragma unroll
-      for (int j = 0; j < N; ++j) v = fma(A.a[bb * N + j], in[j], v);
-      B0[lo + N * bb + N2 * hi] = v;
-    }
+    for (int bb = 0; bb < N; ++bb) B0[lo + N * bb + N2 * hi] = out[bb];
   }
   __syncthreads();
   // pass 3 (x3): y[c][j][i] = s sum_k A[c][k] B0[k][j][i]; thread (i, j) = (lo, hi)
   if (act) {
     const double s = use_d0 ? metric[uniform ? 0 : 4 * e] : 1.0;
-    double in[N];
+    double in[N], out[N];
 #pragma unroll
     for (int k = 0; k < N; ++k) in[k] = B0[lo + N * hi + N2 * k];
+    line_transform<N, PAR>(A, in, out);
     double* ye = y + r * stride + e * N3;
 #pragma unroll
-    for (int cc = 0; cc < N; ++cc) {
-      double v = 0.0;
-#pragma unroll
-      for (int k = 0; k < N; ++k) v = fma(A.a[cc * N + k], in[k], v);
-      ye[lo + N * hi + N2 * cc] = s * v;
-    }
+    for (int cc = 0; cc < N; ++cc) ye[lo + N * hi + N2 * cc] = s * out[cc];
   }
 }
 
@@ -382,6 +425,7 @@ __global__ void cg_init_kernel(CgScalars* cg, int* flags, const double* rr, cons
   CgScalars c;
   c.rr = rr[r];
   c.rr_stop = tol[r] * tol[r] * c.rr;
+  c.rr_old = 0.0;
   c.alpha = 0.0;
   c.beta = 0.0;
   c.it = 0;
@@ -393,79 +437,106 @@ __global__ void cg_init_kernel(CgScalars* cg, int* flags, const double* rr, cons
   flags[r] = c.done;
 }
 
+// One iteration of the single-reduction preconditioned CG of Chronopoulos
+// and Gear, after the operator launch w_i = K u_i that also produced
+// delta_i = u_i . w_i.  With gamma_i = r_i . u_i from the previous step:
+//   beta_i  = gamma_i / gamma_{i-1}                 (0 in the first step)
+//   alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1})
+//   p_i = u_i + beta_i p_{i-1},  s_i = w_i + beta_i s_{i-1}   (s_i = K p_i)
+//   x_{i+1} = x_i + alpha_i p_i,  r_{i+1} = r_i - alpha_i s_i
+//   u_{i+1} = W r_{i+1},  gamma_{i+1} = r_{i+1} . u_{i+1}
+// In exact arithmetic these are the iterates of the standard preconditioned
+// CG; the two inner products of an iteration meet in one reduction phase, so
+// an iteration is two kernels (operator, this update).  w is zeroed for the
+// next operator launch, which accumulates into it.
 template <typename T>
-__global__ void cg_update_kernel(CgScalars* cg, int* flags, const double* __restrict__ pq,
-                                 T* __restrict__ d, T* __restrict__ rvec, const T* __restrict__ p,
-                                 T* __restrict__ q, const T* __restrict__ w, long long len,
-                                 double* partials, unsigned int* counter) {
+__global__ void cg_step_kernel(CgScalars* cg, int* flags, const double* __restrict__ uw,
+                               T* __restrict__ x, T* __restrict__ rvec, T* __restrict__ u,
+                               T* __restrict__ wv, T* __restrict__ p, T* __restrict__ sv,
+                               const T* __restrict__ W, long long len, double* partials,
+                               unsigned int* counter) {
   const int r = blockIdx.y;
   if (flags[r]) return;
   // scalars once per block: FP64 division is slow on this part
-  __shared__ double s_alpha;
+  __shared__ double s_alpha, s_beta;
   __shared__ bool s_bad;
-  __shared__ T s_al;
-  const double rr = cg[r].rr;
+  const double gam = cg[r].rr;
   if (threadIdx.x == 0) {
-    const double pqv = pq[r];
-    s_bad = !(pqv > 0.0) || !(rr == rr) || !(pqv == pqv) || pqv > DBL_MAX;
-    s_alpha = s_bad ? 0.0 : rr / pqv;
-    s_al = static_cast<T>(s_alpha);
+    const CgScalars c = cg[r];
+    const double del = uw[r];
+    const bool first = c.it == 0;
+    const double beta = first ? 0.0 : gam / c.rr_old;
+    const double den = first ? del : del - beta * gam / c.alpha;
+    const bool bad = !(den > 0.0) || !(den <= DBL_MAX) || !(gam == gam);
+    s_bad = bad;
+    s_alpha = bad ? 0.0 : gam / den;
+    s_beta = bad ? 0.0 : beta;
   }
   __syncthreads();
   const bool bad = s_bad;
-  const double alpha = s_alpha;
-  const T al = s_al;
-  T* __restrict__ dr = d + r * len;
-  T* __restrict__ rv = rvec + r * len;
-  const T* __restrict__ pr = p + r * len;
-  T* __restrict__ qr = q + r * len;
-  const T* __restrict__ wr = w ? w + r * len : nullptr;
+  const double alpha = s_alpha, beta = s_beta;
+  const T al = static_cast<T>(alpha), be = static_cast<T>(beta);
+  const long long o = r * len;
   T acc = T(0);
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nvec = (len % 4 == 0) ? len / 4 : 0;
+  const T zero[4] = {T(0), T(0), T(0), T(0)};
   for (long long v = tid; v < nvec; v += stride) {
-    const long long t = 4 * v;
-    T pv[4], dv[4], qv[4], rn[4], wv[4] = {T(1), T(1), T(1), T(1)};
-    const T zero[4] = {T(0), T(0), T(0), T(0)};
-    ld4(pr + t, pv);
-    ld4(dr + t, dv);
-    ld4(qr + t, qv);
-    ld4(rv + t, rn);
-    if (wr) ld4(wr + t, wv);
+    const long long t = o + 4 * v;
+    T uv[4], wq[4], pv[4], sq[4], xv[4], rv[4], mv[4] = {T(1), T(1), T(1), T(1)};
+    ld4(u + t, uv);
+    ld4(wv + t, wq);
+    ld4(p + t, pv);
+    ld4(sv + t, sq);
+    ld4(x + t, xv);
+    ld4(rvec + t, rv);
+    if (W) ld4(W + t, mv);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      dv[k] = fma(al, pv[k], dv[k]);
-      rn[k] = fma(-al, qv[k], rn[k]);
-      acc = fma(rn[k] * wv[k], rn[k], acc);   // r . z with z = W r
+      pv[k] = fma(be, pv[k], uv[k]);
+      sq[k] = fma(be, sq[k], wq[k]);
+      xv[k] = fma(al, pv[k], xv[k]);
+      rv[k] = fma(-al, sq[k], rv[k]);
+      uv[k] = mv[k] * rv[k];
+      acc = fma(uv[k], rv[k], acc);
     }
-    st4(dr + t, dv);
-    st4(rv + t, rn);
-    st4(qr + t, zero);
+    st4(p + t, pv);
+    st4(sv + t, sq);
+    st4(x + t, xv);
+    st4(rvec + t, rv);
+    st4(u + t, uv);
+    st4(wv + t, zero);
   }
-  for (long long t = nvec * 4 + tid; t < len; t += stride) {
-    const T pv = pr[t], dv = dr[t], qv = qr[t], r0 = rv[t], wv = wr ? wr[t] : T(1);
-    const T rn = fma(-al, qv, r0);
-    dr[t] = fma(al, pv, dv);
-    rv[t] = rn;
-    qr[t] = T(0);
-    acc = fma(rn * wv, rn, acc);
+  for (long long t = o + nvec * 4 + tid; t < o + len; t += stride) {
+    const T pn = fma(be, p[t], u[t]);
+    const T sn = fma(be, sv[t], wv[t]);
+    const T rn = fma(-al, sn, rvec[t]);
+    const T un = (W ? W[t] : T(1)) * rn;
+    x[t] = fma(al, pn, x[t]);
+    p[t] = pn;
+    sv[t] = sn;
+    rvec[t] = rn;
+    u[t] = un;
+    wv[t] = T(0);
+    acc = fma(un, rn, acc);
   }
-  const double s = block_sum(static_cast<double>(acc));
-  if (finish_partial(s, partials, counter, r)) {
-    const double rr_new = sum_partials(partials, r);
+  const double sblk = block_sum(static_cast<double>(acc));
+  if (finish_partial(sblk, partials, counter, r)) {
+    const double gnew = sum_partials(partials, r);
     if (threadIdx.x != 0) return;
     counter[r] = 0u;
     CgScalars c = cg[r];
-    c.alpha = alpha;
     c.it += 1;
-    if (bad || !(rr_new == rr_new)) {
+    if (bad || !(gnew == gnew)) {
       c.status = 6;
       c.done = 1;
     } else {
-      c.beta = rr_new / rr;
-      c.rr = rr_new;
-      if (rr_new <= c.rr_stop) c.done = 1;
+      c.rr_old = gam;
+      c.rr = gnew;
+      c.alpha = alpha;
+      c.beta = beta;
+      if (gnew <= c.rr_stop) c.done = 1;
       else if (c.it >= c.max_it) { c.done = 1; c.status = 5; }
     }
     cg[r] = c;
@@ -519,20 +590,49 @@ cudaError_t ft_one(const TI* x, TO* y, long long nfaces, int nrhs, long long sx,
   return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t vt_one(const double* x, double* y, long long nelem, int nrhs, long long stride,
-                   const Mat1D<double>& A, const double* metric, int uniform, int use_d0,
-                   cudaStream_t s) {
+// Mirror-symmetry form of A (see line_transform): 1 rows, 2 columns, 0 none.
+// Checked to a relative 1e-13 of the largest entry; the parity kernels then
+// use only the first half of each row or column.
+int matrix_parity(int n, const Mat1D<double>& A) {
+  const int ne = (n + 1) / 2;
+  double amax = 0.0;
+  for (int i = 0; i < n * n; ++i) amax = fmax(amax, fabs(A.a[i]));
+  const double tol = 1e-13 * amax;
+  bool row = true, col = true;
+  for (int a = 0; a < n; ++a)
+    for (int i = 0; i < n; ++i) {
+      const double sa = a < ne ? 1.0 : -1.0, si = i < ne ? 1.0 : -1.0;
+      row = row && fabs(A.a[a * n + (n - 1 - i)] - sa * A.a[a * n + i]) <= tol;
+      col = col && fabs(A.a[(n - 1 - a) * n + i] - si * A.a[a * n + i]) <= tol;
+    }
+  return row ? 1 : (col ? 2 : 0);
+}
+
+template <int N, int PAR>
+cudaError_t vt_launch(const double* x, double* y, long long nelem, int nrhs, long long stride,
+                      const Mat1D<double>& A, const double* metric, int uniform, int use_d0,
+                      cudaStream_t s) {
   const int epb = (256 / (N * N)) > 0 ? 256 / (N * N) : 1;
   const int threads = (epb * N * N + 31) / 32 * 32;
   const size_t smem = (size_t)epb * 2 * N * N * N * sizeof(double);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(volume_transform_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(volume_transform_kernel<N, PAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)((nelem + epb - 1) / epb), nrhs);
   if (nelem <= 0) return cudaSuccess;
-  volume_transform_kernel<N><<<grid, threads, smem, s>>>(x, y, nelem, stride, A, metric, uniform,
-                                                        use_d0, epb);
+  volume_transform_kernel<N, PAR><<<grid, threads, smem, s>>>(x, y, nelem, stride, A, metric, uniform,
+                                                             use_d0, epb);
   return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t vt_one(const double* x, double* y, long long nelem, int nrhs, long long stride,
+                   const Mat1D<double>& A, const double* metric, int uniform, int use_d0,
+                   cudaStream_t s) {
+  switch (matrix_parity(N, A)) {
+    case 1: return vt_launch<N, 1>(x, y, nelem, nrhs, stride, A, metric, uniform, use_d0, s);
+    case 2: return vt_launch<N, 2>(x, y, nelem, nrhs, stride, A, metric, uniform, use_d0, s);
+    default: return vt_launch<N, 0>(x, y, nelem, nrhs, stride, A, metric, uniform, use_d0, s);
+  }
 }
 
 }  // namespace
@@ -654,19 +754,19 @@ cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, const do
 }
 
 template <typename T>
-cudaError_t launch_cg_update(CgScalars* cg, int* flags, const double* pq, T* d, T* r, const T* p,
-                             T* q, const T* w, long long len, int nrhs, double* partials,
-                             unsigned int* counter, int blocks, cudaStream_t s) {
+cudaError_t launch_cg_step(CgScalars* cg, int* flags, const double* uw, T* x, T* r, T* u, T* w, T* p, T* sv,
+                           const T* W, long long len, int nrhs, double* partials, unsigned int* counter,
+                           int blocks, cudaStream_t s) {
   dim3 grid(blocks, nrhs);
-  cg_update_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, pq, d, r, p, q, w, len, partials, counter);
+  cg_step_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, uw, x, r, u, w, p, sv, W, len, partials, counter);
   return cudaGetLastError();
 }
-template cudaError_t launch_cg_update<double>(CgScalars*, int*, const double*, double*, double*,
-                                              const double*, double*, const double*, long long, int,
-                                              double*, unsigned int*, int, cudaStream_t);
-template cudaError_t launch_cg_update<float>(CgScalars*, int*, const double*, float*, float*,
-                                             const float*, float*, const float*, long long, int,
-                                             double*, unsigned int*, int, cudaStream_t);
+template cudaError_t launch_cg_step<double>(CgScalars*, int*, const double*, double*, double*, double*, double*,
+                                            double*, double*, const double*, long long, int, double*,
+                                            unsigned int*, int, cudaStream_t);
+template cudaError_t launch_cg_step<float>(CgScalars*, int*, const double*, float*, float*, float*, float*,
+                                           float*, float*, const float*, long long, int, double*,
+                                           unsigned int*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w, long long len, int nrhs,

@@ -6,7 +6,7 @@
 namespace hdg {
 namespace {
 
-template <int N, bool DZC, bool FUSEP = false>
+template <int N, bool DZC>
 int fast_occupancy(int ppb) {
   static int cached[65] = {0};
   const int key = ppb < 64 ? ppb : 64;
@@ -14,9 +14,9 @@ int fast_occupancy(int ppb) {
   const int threads = tpt_threads(N, ppb);
   const size_t smem = (size_t)ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
   if (smem > 48 * 1024)
-    cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, FUSEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(tpt_fast_kernel<N, DZC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpt_fast_kernel<N, DZC, FUSEP>, threads, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpt_fast_kernel<N, DZC>, threads, smem) !=
           cudaSuccess ||
       nb < 1) {
     cudaGetLastError();
@@ -26,29 +26,29 @@ int fast_occupancy(int ppb) {
   return nb;
 }
 
-template <int N, bool DZC, bool FUSEP>
+template <int N, bool DZC>
 cudaError_t fast_launch(const TptArgs<float, float>& a, int nrhs, cudaStream_t s) {
-  if (a.npencils <= 0) return cudaSuccess;
-  if (a.seg < 1 || a.nseg < 1) return cudaErrorInvalidValue;
+  const long long nelem = a.npencils * a.mesh.ne[0];
+  if (nelem <= 0) return cudaSuccess;
+  if (a.chunk < 1 || a.ppb < 1) return cudaErrorInvalidValue;
   const int threads = tpt_threads(N, a.ppb);
   const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
-  if (threads > 320) return cudaErrorInvalidConfiguration;
+  if (threads > fast_max_threads(N)) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, FUSEP>,
+    cudaError_t e = cudaFuncSetAttribute(tpt_fast_kernel<N, DZC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  long long blocks = tpt_blocks(a.npencils * a.nseg, a.ppb);
-  if (a.max_grid > 0 && blocks > a.max_grid) blocks = a.max_grid;
+  // one run of `chunk` elements per slot: every element is covered exactly once
+  const long long blocks = (nelem + (long long)a.chunk * a.ppb - 1) / ((long long)a.chunk * a.ppb);
   dim3 grid((unsigned)blocks, (unsigned)nrhs);
-  tpt_fast_kernel<N, DZC, FUSEP><<<grid, threads, smem, s>>>(a);
+  tpt_fast_kernel<N, DZC><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t fast_dispatch_dz(const TptArgs<float, float>& a, int nrhs, cudaStream_t s) {
-  if (a.cg) return a.dinv ? fast_launch<N, false, true>(a, nrhs, s) : fast_launch<N, true, true>(a, nrhs, s);
-  return a.dinv ? fast_launch<N, false, false>(a, nrhs, s) : fast_launch<N, true, false>(a, nrhs, s);
+  return a.dinv ? fast_launch<N, false>(a, nrhs, s) : fast_launch<N, true>(a, nrhs, s);
 }
 
 #define FAST_N_SWITCH(n, CALL)                                                  \

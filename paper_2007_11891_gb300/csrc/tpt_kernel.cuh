@@ -69,17 +69,11 @@ struct TptArgs {
   long long npencils;           // ne[1] * ne[2]
   int seg;                      // elements per pencil segment (x1 direction)
   int nseg;                     // segments per pencil = ceil(ne[0] / seg)
+  int chunk;                    // FP32 apply kernel: elements per slot (a contiguous run
+                                // in element order, possibly spanning x1-pencils)
   int max_grid;                 // CTAs launched (grid-stride over slot groups); 0 = one per group
   const int* skip;              // per rhs: nonzero -> do nothing (converged), or null
   CgHook hook;                  // partials == null: no dot
-  // fused search-direction update (FP32 apply only): when cg is set, the
-  // operator input is p_new = W r + beta p_old with p_old = x, r = pr,
-  // W = pw (null: identity), beta = cg[rhs].beta; p_new is written to pout
-  // by exactly one owner slot per face
-  const CgScalars* cg;
-  const ST* pr;
-  const ST* pw;
-  ST* pout;
 };
 
 // Shared memory per pencil slot (elements of T): two buffers of the four
@@ -89,6 +83,13 @@ template <typename T, int N>
 __host__ __device__ constexpr int tpt_smem_per_pencil() {
   return 2 * 4 * N * dz_row(N, sizeof(T)) + N * N * dz_row(N, sizeof(T));
 }
+
+// FP32 apply kernel (tpt_fast.cuh): CTA size limit and guaranteed resident
+// CTAs per SM.  256 threads (256 / n^2 element slots) and three CTAs (at
+// most 80 registers) for n <= 16, which measured 16% faster than two CTAs
+// with more registers; n = 17 needs 289 threads per slot.
+__host__ __device__ constexpr int fast_max_threads(int n) { return n * n > 256 ? 320 : 256; }
+__host__ __device__ constexpr int fast_min_ctas(int n) { return n * n > 256 ? 2 : 3; }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
