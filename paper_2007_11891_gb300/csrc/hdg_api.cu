@@ -279,8 +279,8 @@ int reduction_blocks(long long len) {
 
 hdg_status ensure_reductions(hdg_ctx* c, int nrhs) {
   c->red_blocks = 152 * 8;   // upper bound on blocks of any reducing vector launch
-  // the operator grid is largest when every pencil is split into single elements
-  const long long tpt_b = hdg::tpt_blocks(c->nelem, hdg::tpt_ppb(c->n));
+  // the operator grid is largest with one element per CTA (one slot, runs of one)
+  const long long tpt_b = c->nelem;
   const long long pb = std::max<long long>(c->red_blocks, tpt_b);
   HDG_TRY(ensure(c->partials, sizeof(double) * (size_t)nrhs * pb));
   const bool fresh = c->counters.bytes < sizeof(unsigned int) * (size_t)nrhs;
@@ -356,16 +356,15 @@ hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, 
   int* flags = static_cast<int*>(c->flags.p);
   hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
   double* uw = static_cast<double*>(c->scal.p) + nrhs;
-  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), uw};
+  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), uw, cg};
   T* u = wsp<T>(c, W_U);
   T* sv = wsp<T>(c, W_S);
-  const int vb = reduction_blocks(T_);
+  const int vb = hdg::cg_step_blocks<T>(T_);
   for (int k = 0; k < count; ++k) {
     HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, u, q, s, flags, hook, true)));
     Timed t_(c, K_VEC, s);
-    HDG_CUDA(hdg::launch_cg_step<T>(cg, flags, uw, d, r, u, q, p, sv, w, T_, nrhs,
-                                    static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p),
-                                    vb, s));
+    HDG_CUDA(hdg::launch_cg_step<T>(cg, flags, d, r, u, q, p, sv, w, T_, nrhs, static_cast<double*>(c->partials.p),
+                                    static_cast<unsigned int*>(c->counters.p), vb, s));
   }
   return HDG_OK;
 }
@@ -1115,7 +1114,12 @@ hdg_status hdg_apply(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precision
                                                         c->ntrace, c->ntrace, c->MS, 1.0, 0, s))); }
     return HDG_OK;
   }
-  return fail(HDG_ERR_UNSUPPORTED, "BF16 apply is not available");
+  // BF16-stored traces, FP32 arithmetic, transformed basis
+  if (basis != HDG_BASIS_TRANSFORMED) return fail(HDG_ERR_INVALID_ARG, "BF16 apply is available in the transformed basis only");
+  const float* dinv = nullptr;
+  HDG_TRY(ensure_dinv<float>(c, nrhs, h_lambda, s, &dinv));
+  return tpt_apply<float, __nv_bfloat16>(c, nrhs, dinv, static_cast<const __nv_bfloat16*>(d_x),
+                                         static_cast<__nv_bfloat16*>(d_y), s);
 }
 
 hdg_status hdg_solve(hdg_ctx* c, int nrhs, const double* h_lambda, const double* d_f, const double* d_bdry,

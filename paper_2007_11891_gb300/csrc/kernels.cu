@@ -1,5 +1,6 @@
 // Face and volume tensor-product transforms, D_Z^-1 tables, vector kernels
 // and the CG scalar updates of the condensed HDG library.
+#include <algorithm>
 #include <cfloat>
 
 #include "internal.h"
@@ -438,50 +439,31 @@ __global__ void cg_init_kernel(CgScalars* cg, int* flags, const double* rr, cons
 }
 
 // One iteration of the single-reduction preconditioned CG of Chronopoulos
-// and Gear, after the operator launch w_i = K u_i that also produced
-// delta_i = u_i . w_i.  With gamma_i = r_i . u_i from the previous step:
-//   beta_i  = gamma_i / gamma_{i-1}                 (0 in the first step)
-//   alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1})
+// and Gear, after the operator launch w_i = K u_i, whose last block already
+// turned delta_i = u_i . w_i into the step scalars (cg_scalars):
 //   p_i = u_i + beta_i p_{i-1},  s_i = w_i + beta_i s_{i-1}   (s_i = K p_i)
 //   x_{i+1} = x_i + alpha_i p_i,  r_{i+1} = r_i - alpha_i s_i
 //   u_{i+1} = W r_{i+1},  gamma_{i+1} = r_{i+1} . u_{i+1}
 // In exact arithmetic these are the iterates of the standard preconditioned
 // CG; the two inner products of an iteration meet in one reduction phase, so
 // an iteration is two kernels (operator, this update).  w is zeroed for the
-// next operator launch, which accumulates into it.
+// next operator launch, which accumulates into it.  Every thread issues all
+// loads of its entries before it reads the scalars (no barrier before the
+// streams start); one resident wave of blocks covers the vectors.
 template <typename T>
-__global__ void cg_step_kernel(CgScalars* cg, int* flags, const double* __restrict__ uw,
-                               T* __restrict__ x, T* __restrict__ rvec, T* __restrict__ u,
-                               T* __restrict__ wv, T* __restrict__ p, T* __restrict__ sv,
-                               const T* __restrict__ W, long long len, double* partials,
-                               unsigned int* counter) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) cg_step_kernel(CgScalars* cg, int* flags, T* __restrict__ x,
+                                                        T* __restrict__ rvec, T* __restrict__ u,
+                                                        T* __restrict__ wv, T* __restrict__ p,
+                                                        T* __restrict__ sv, const T* __restrict__ W,
+                                                        long long len, double* partials, unsigned int* counter) {
   const int r = blockIdx.y;
   if (flags[r]) return;
-  // scalars once per block: FP64 division is slow on this part
-  __shared__ double s_alpha, s_beta;
-  __shared__ bool s_bad;
-  const double gam = cg[r].rr;
-  if (threadIdx.x == 0) {
-    const CgScalars c = cg[r];
-    const double del = uw[r];
-    const bool first = c.it == 0;
-    const double beta = first ? 0.0 : gam / c.rr_old;
-    const double den = first ? del : del - beta * gam / c.alpha;
-    const bool bad = !(den > 0.0) || !(den <= DBL_MAX) || !(gam == gam);
-    s_bad = bad;
-    s_alpha = bad ? 0.0 : gam / den;
-    s_beta = bad ? 0.0 : beta;
-  }
-  __syncthreads();
-  const bool bad = s_bad;
-  const double alpha = s_alpha, beta = s_beta;
-  const T al = static_cast<T>(alpha), be = static_cast<T>(beta);
   const long long o = r * len;
-  T acc = T(0);
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nvec = (len % 4 == 0) ? len / 4 : 0;
   const T zero[4] = {T(0), T(0), T(0), T(0)};
+  T acc = T(0);
   for (long long v = tid; v < nvec; v += stride) {
     const long long t = o + 4 * v;
     T uv[4], wq[4], pv[4], sq[4], xv[4], rv[4], mv[4] = {T(1), T(1), T(1), T(1)};
@@ -492,6 +474,7 @@ __global__ void cg_step_kernel(CgScalars* cg, int* flags, const double* __restri
     ld4(x + t, xv);
     ld4(rvec + t, rv);
     if (W) ld4(W + t, mv);
+    const T al = static_cast<T>(cg[r].alpha), be = static_cast<T>(cg[r].beta);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       pv[k] = fma(be, pv[k], uv[k]);
@@ -508,18 +491,21 @@ __global__ void cg_step_kernel(CgScalars* cg, int* flags, const double* __restri
     st4(u + t, uv);
     st4(wv + t, zero);
   }
-  for (long long t = o + nvec * 4 + tid; t < o + len; t += stride) {
-    const T pn = fma(be, p[t], u[t]);
-    const T sn = fma(be, sv[t], wv[t]);
-    const T rn = fma(-al, sn, rvec[t]);
-    const T un = (W ? W[t] : T(1)) * rn;
-    x[t] = fma(al, pn, x[t]);
-    p[t] = pn;
-    sv[t] = sn;
-    rvec[t] = rn;
-    u[t] = un;
-    wv[t] = T(0);
-    acc = fma(un, rn, acc);
+  {
+    const T al = static_cast<T>(cg[r].alpha), be = static_cast<T>(cg[r].beta);
+    for (long long t = o + nvec * 4 + tid; t < o + len; t += stride) {
+      const T pn = fma(be, p[t], u[t]);
+      const T sn = fma(be, sv[t], wv[t]);
+      const T rn = fma(-al, sn, rvec[t]);
+      const T un = (W ? W[t] : T(1)) * rn;
+      x[t] = fma(al, pn, x[t]);
+      p[t] = pn;
+      sv[t] = sn;
+      rvec[t] = rn;
+      u[t] = un;
+      wv[t] = T(0);
+      acc = fma(un, rn, acc);
+    }
   }
   const double sblk = block_sum(static_cast<double>(acc));
   if (finish_partial(sblk, partials, counter, r)) {
@@ -528,14 +514,12 @@ __global__ void cg_step_kernel(CgScalars* cg, int* flags, const double* __restri
     counter[r] = 0u;
     CgScalars c = cg[r];
     c.it += 1;
-    if (bad || !(gnew == gnew)) {
+    if (c.status == 6 || !(gnew == gnew)) {
       c.status = 6;
       c.done = 1;
     } else {
-      c.rr_old = gam;
+      c.rr_old = c.rr;
       c.rr = gnew;
-      c.alpha = alpha;
-      c.beta = beta;
       if (gnew <= c.rr_stop) c.done = 1;
       else if (c.it >= c.max_it) { c.done = 1; c.status = 5; }
     }
@@ -754,19 +738,39 @@ cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, const do
 }
 
 template <typename T>
-cudaError_t launch_cg_step(CgScalars* cg, int* flags, const double* uw, T* x, T* r, T* u, T* w, T* p, T* sv,
-                           const T* W, long long len, int nrhs, double* partials, unsigned int* counter,
-                           int blocks, cudaStream_t s) {
+int cg_step_blocks(long long len) {
+  static int per_sm = 0;
+  static int sms = 0;
+  if (per_sm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 152;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_step_kernel<T>, kVecThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    cudaGetLastError();
+  }
+  const long long need = (len / 4 + kVecThreads - 1) / kVecThreads;
+  return (int)std::max(1LL, std::min(need, (long long)sms * per_sm));
+}
+
+template <typename T>
+cudaError_t launch_cg_step(CgScalars* cg, int* flags, T* x, T* r, T* u, T* w, T* p, T* sv, const T* W,
+                           long long len, int nrhs, double* partials, unsigned int* counter, int blocks,
+                           cudaStream_t s) {
   dim3 grid(blocks, nrhs);
-  cg_step_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, uw, x, r, u, w, p, sv, W, len, partials, counter);
+  cg_step_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, x, r, u, w, p, sv, W, len, partials, counter);
   return cudaGetLastError();
 }
-template cudaError_t launch_cg_step<double>(CgScalars*, int*, const double*, double*, double*, double*, double*,
-                                            double*, double*, const double*, long long, int, double*,
-                                            unsigned int*, int, cudaStream_t);
-template cudaError_t launch_cg_step<float>(CgScalars*, int*, const double*, float*, float*, float*, float*,
-                                           float*, float*, const float*, long long, int, double*,
-                                           unsigned int*, int, cudaStream_t);
+template int cg_step_blocks<double>(long long);
+template int cg_step_blocks<float>(long long);
+template cudaError_t launch_cg_step<double>(CgScalars*, int*, double*, double*, double*, double*, double*,
+                                            double*, const double*, long long, int, double*, unsigned int*,
+                                            int, cudaStream_t);
+template cudaError_t launch_cg_step<float>(CgScalars*, int*, float*, float*, float*, float*, float*, float*,
+                                           const float*, long long, int, double*, unsigned int*, int,
+                                           cudaStream_t);
 
 template <typename T>
 cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w, long long len, int nrhs,

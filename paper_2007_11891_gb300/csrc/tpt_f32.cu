@@ -26,8 +26,8 @@ int fast_occupancy(int ppb) {
   return nb;
 }
 
-template <int N, bool DZC>
-cudaError_t fast_launch(const TptArgs<float, float>& a, int nrhs, cudaStream_t s) {
+template <int N, bool DZC, typename ST>
+cudaError_t fast_launch(const TptArgs<float, ST>& a, int nrhs, cudaStream_t s) {
   const long long nelem = a.npencils * a.mesh.ne[0];
   if (nelem <= 0) return cudaSuccess;
   if (a.chunk < 1 || a.ppb < 1) return cudaErrorInvalidValue;
@@ -35,20 +35,20 @@ cudaError_t fast_launch(const TptArgs<float, float>& a, int nrhs, cudaStream_t s
   const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
   if (threads > fast_max_threads(N)) return cudaErrorInvalidConfiguration;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(tpt_fast_kernel<N, DZC>,
+    cudaError_t e = cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   // one run of `chunk` elements per slot: every element is covered exactly once
   const long long blocks = (nelem + (long long)a.chunk * a.ppb - 1) / ((long long)a.chunk * a.ppb);
   dim3 grid((unsigned)blocks, (unsigned)nrhs);
-  tpt_fast_kernel<N, DZC><<<grid, threads, smem, s>>>(a);
+  tpt_fast_kernel<N, DZC, ST><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <int N>
-cudaError_t fast_dispatch_dz(const TptArgs<float, float>& a, int nrhs, cudaStream_t s) {
-  return a.dinv ? fast_launch<N, false>(a, nrhs, s) : fast_launch<N, true>(a, nrhs, s);
+template <int N, typename ST>
+cudaError_t fast_dispatch_dz(const TptArgs<float, ST>& a, int nrhs, cudaStream_t s) {
+  return a.dinv ? fast_launch<N, false, ST>(a, nrhs, s) : fast_launch<N, true, ST>(a, nrhs, s);
 }
 
 #define FAST_N_SWITCH(n, CALL)                                                  \
@@ -79,12 +79,28 @@ int tpt_blocks_per_sm<float, float>(int mode, int n, int ppb) {
 template <>
 cudaError_t launch_tpt<float, float>(int mode, int n, TptArgs<float, float> a, int nrhs, cudaStream_t s) {
   if (mode == TPT_APPLY) {
-#define FL(N) fast_dispatch_dz<N>(a, nrhs, s)
+#define FL(N) fast_dispatch_dz<N, float>(a, nrhs, s)
     FAST_N_SWITCH(n, FL)
 #undef FL
     return cudaErrorInvalidValue;
   }
   return tpt_dispatch<float, float>(mode, n, a, nrhs, s);
+}
+
+// BF16-stored traces: the apply only (FP32 arithmetic, same kernel)
+template <>
+int tpt_blocks_per_sm<float, __nv_bfloat16>(int mode, int n, int ppb) {
+  return tpt_blocks_per_sm<float, float>(mode, n, ppb);
+}
+
+template <>
+cudaError_t launch_tpt<float, __nv_bfloat16>(int mode, int n, TptArgs<float, __nv_bfloat16> a, int nrhs,
+                                             cudaStream_t s) {
+  if (mode != TPT_APPLY) return cudaErrorInvalidValue;
+#define FLB(N) fast_dispatch_dz<N, __nv_bfloat16>(a, nrhs, s)
+  FAST_N_SWITCH(n, FLB)
+#undef FLB
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace hdg

@@ -15,10 +15,12 @@
 // red.global.add contributions (two adds onto zero commute exactly, so the
 // result does not depend on how the elements are split into runs).
 //
-// Specialised for the hot path: FP32 storage and arithmetic, homogeneous
-// Dirichlet data, D_Z^-1 source fixed at compile time (DZC: computed in the
-// kernel; else a table), 32-bit offsets (trace size < 2^31 per right-hand
-// side, checked on the host).
+// Specialised for the hot path: FP32 arithmetic, homogeneous Dirichlet data,
+// D_Z^-1 source fixed at compile time (DZC: computed in the kernel; else a
+// table), 32-bit offsets (trace size < 2^31 per right-hand side, checked on
+// the host).  Trace storage ST: float, or bfloat16 (inputs widened to FP32;
+// every output contribution rounded to BF16 and added with a BF16 atomic, so
+// that, here too, each face value is the same two-term sum whatever the runs).
 #pragma once
 
 #include "tpt_kernel.cuh"
@@ -31,9 +33,13 @@ struct FaceOffsets {
   int x1l, x1h, x2l, x2h, x3l, x3h;
 };
 
-template <int N, bool DZC>
+template <int N, bool DZC, typename ST = float>
 __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
-    tpt_fast_kernel(const TptArgs<float, float> a) {
+    tpt_fast_kernel(const TptArgs<float, ST> a) {
+  // FP32 storage sums the x1-face between consecutive elements of a run in
+  // registers; BF16 storage adds both contributions atomically (a register
+  // sum would round once where the atomics round twice)
+  constexpr bool kCarry = std::is_same<ST, float>::value;
   constexpr int N2 = N * N, NE = (N + 1) / 2;
   constexpr int R = dz_row(N, sizeof(float));
   constexpr int NQ = R / 4;
@@ -60,8 +66,8 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   const int lo0 = m.lo[0], hi0 = m.hi[0], lo1 = m.lo[1], hi1 = m.hi[1], lo2 = m.lo[2], hi2 = m.hi[2];
   const int blk0 = (int)m.blk[0], blk1 = (int)m.blk[1], blk2 = (int)m.blk[2];
   const long long toff = (long long)rhs * a.trace_stride;
-  const float* __restrict__ xin = a.x + toff;
-  float* __restrict__ yout = a.y + toff;
+  const ST* __restrict__ xin = a.x + toff;
+  ST* __restrict__ yout = a.y + toff;
   const float* __restrict__ dinv_r = DZC ? nullptr : a.dinv + (long long)rhs * a.dinv_rhs_stride;
   const float lam_r = DZC ? static_cast<float>(a.lam[rhs]) : 0.f;
   const float hs = a.tab.h0 + a.tab.h1, hd = a.tab.h0 - a.tab.h1;
@@ -93,7 +99,7 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
     o.x3h = (e3 + 1 >= lo2 && e3 + 1 <= hi2) ? b3 + pl2 * N2 : -1;
     return o;
   };
-  auto ld = [&](int off) -> float { return off >= 0 ? xin[off] : 0.f; };
+  auto ld = [&](int off) -> float { return off >= 0 ? load_as<ST, float>(xin + off) : 0.f; };
 
   FaceOffsets o = offsets(c1, c2, c3);
   float xlo1 = 0.f, xhi1 = 0.f, x2l = 0.f, x2h = 0.f, x3l = 0.f, x3h = 0.f;
@@ -221,18 +227,18 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
         // lo plane: the previous element of the run left its share in
         // `carry`; plane 0 has no other contributor; else another run adds
         if (o.x1l >= 0) {
-          if (have_carry) yout[o.x1l] = carry + rlo;
-          else if (c1 == 0) yout[o.x1l] = rlo;
+          if (have_carry) store_from<ST, float>(yout + o.x1l, carry + rlo);
+          else if (c1 == 0) store_from<ST, float>(yout + o.x1l, rlo);
           else red_add(yout + o.x1l, rlo);
         }
         // hi plane: kept for the next element of the run; the top plane has
         // no other contributor; else another run adds
-        if (o.x1h >= 0 && !same) {
-          if (c1 + 1 == N1e) yout[o.x1h] = rhi;
+        if (o.x1h >= 0 && !(kCarry && same)) {
+          if (c1 + 1 == N1e) store_from<ST, float>(yout + o.x1h, rhi);
           else red_add(yout + o.x1h, rhi);
         }
         carry = rhi;
-        have_carry = same;
+        have_carry = kCarry && same;
       }
     }
     o = no;
@@ -242,39 +248,7 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
     x2l = n2l; x2h = n2h; x3l = n3l; x3h = n3h;
   }
 
-  if (a.hook.partials != nullptr) {
-    // x^T y = 1/2 sum over element faces of (S sum + D dif); last block sums
-    __shared__ double wsum[16];
-    __shared__ bool last;
-    const float v = warp_sum(dot);
-    if ((tid & 31) == 0) wsum[tid >> 5] = (double)v;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) s += wsum[w];
-      a.hook.partials[(long long)rhs * gridDim.x + blockIdx.x] = 0.5 * s;
-      __threadfence();
-      const unsigned int done = atomicAdd(a.hook.counter + rhs, 1u);
-      last = (done == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last) {
-      __threadfence();
-      const volatile double* pp = a.hook.partials + (long long)rhs * gridDim.x;
-      double s = 0.0;
-      for (unsigned int b = tid; b < gridDim.x; b += blockDim.x) s += pp[b];
-      s = warp_sum(s);
-      __syncthreads();
-      if ((tid & 31) == 0) wsum[tid >> 5] = s;
-      __syncthreads();
-      if (tid == 0) {
-        double tt = 0.0;
-        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tt += wsum[w];
-        a.hook.pq[rhs] = tt;
-        a.hook.counter[rhs] = 0u;
-      }
-    }
-  }
+  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot);
 }
 
 }  // namespace hdg

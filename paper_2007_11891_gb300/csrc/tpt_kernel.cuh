@@ -46,7 +46,74 @@ struct CgHook {
   double* partials;        // [nrhs][gridDim.x]
   unsigned int* counter;   // [nrhs], zero between launches
   double* pq;              // [nrhs] result: x^T K x
+  CgScalars* cg;           // non-null: also the step scalars of the CG (cg_scalars)
 };
+
+// Step scalars of the single-reduction CG (Chronopoulos-Gear) once
+// delta_i = u_i^T K u_i is known, with gamma_i = rr, gamma_{i-1} = rr_old and
+// alpha_{i-1} = alpha of the previous step:
+//   beta_i = gamma_i / gamma_{i-1} (0 in the first step),
+//   alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1}).
+// A non-positive or non-finite denominator is a breakdown: status 6 and
+// zero steps (the update kernel then stops this right-hand side).
+__device__ __forceinline__ void cg_scalars(CgScalars* cgp, double delta) {
+  CgScalars c = *cgp;
+  if (c.done) return;
+  const bool first = c.it == 0;
+  const double gam = c.rr;
+  const double beta = first ? 0.0 : gam / c.rr_old;
+  const double den = first ? delta : delta - beta * gam / c.alpha;
+  const bool bad = !(den > 0.0) || !(den <= 1.79e308) || !(gam == gam);
+  cgp->alpha = bad ? 0.0 : gam / den;
+  cgp->beta = bad ? 0.0 : beta;
+  if (bad) cgp->status = 6;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// End of an operator launch with a hook: x^T y = 1/2 sum over element faces
+// of (S sum + D dif) from every thread's `dot`; the last block to finish sums
+// the per-block partials in a fixed order (deterministic) and stores the
+// result (and the CG step scalars when hook.cg is set).
+__device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, double dot) {
+  __shared__ double wsum[16];
+  __shared__ bool last;
+  const int tid = threadIdx.x;
+  const double v = warp_sum(dot);
+  if ((tid & 31) == 0) wsum[tid >> 5] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) s += wsum[w];
+    hook.partials[(long long)rhs * gridDim.x + blockIdx.x] = 0.5 * s;
+    __threadfence();
+    const unsigned int done = atomicAdd(hook.counter + rhs, 1u);
+    last = (done == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    const volatile double* pp = hook.partials + (long long)rhs * gridDim.x;
+    double s = 0.0;
+    for (unsigned int b = tid; b < gridDim.x; b += blockDim.x) s += pp[b];
+    s = warp_sum(s);
+    __syncthreads();
+    if ((tid & 31) == 0) wsum[tid >> 5] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += wsum[w];
+      hook.pq[rhs] = t;
+      hook.counter[rhs] = 0u;
+      if (hook.cg) cg_scalars(hook.cg + rhs, t);
+    }
+  }
+}
 
 template <typename T, typename ST>
 struct TptArgs {
@@ -91,12 +158,6 @@ __host__ __device__ constexpr int tpt_smem_per_pencil() {
 __host__ __device__ constexpr int fast_max_threads(int n) { return n * n > 256 ? 320 : 256; }
 __host__ __device__ constexpr int fast_min_ctas(int n) { return n * n > 256 ? 2 : 3; }
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // At most 320 threads per CTA (n = 17: 289 threads rounded to warps).  FP32
 // instantiations keep three resident CTAs per SM (64 registers); FP64 ones
@@ -322,40 +383,7 @@ __global__ void __launch_bounds__(320, sizeof(T) == 4 ? 3 : 2) tpt_kernel(const 
   __syncthreads();   // the next group restages the face buffers
   }  // slot groups
 
-  if (MODE == TPT_APPLY && a.hook.partials != nullptr) {
-    // x^T y = sum over element faces of x . r = 1/2 sum (S sum + D dif)
-    __shared__ double wsum[16];
-    __shared__ bool last;
-    T v = warp_sum(dot);   // idle threads never added to dot
-    if ((tid & 31) == 0) wsum[tid >> 5] = (double)v;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) s += wsum[w];
-      a.hook.partials[(long long)rhs * gridDim.x + blockIdx.x] = 0.5 * s;
-      __threadfence();
-      const unsigned int done = atomicAdd(a.hook.counter + rhs, 1u);
-      last = (done == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (last) {
-      // the last block sums all partials: fixed strided split + fixed tree
-      __threadfence();
-      const volatile double* pp = a.hook.partials + (long long)rhs * gridDim.x;
-      double s = 0.0;
-      for (unsigned int b = tid; b < gridDim.x; b += blockDim.x) s += pp[b];
-      s = warp_sum(s);
-      __syncthreads();
-      if ((tid & 31) == 0) wsum[tid >> 5] = s;
-      __syncthreads();
-      if (tid == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += wsum[w];
-        a.hook.pq[rhs] = t;
-        a.hook.counter[rhs] = 0u;
-      }
-    }
-  }
+  if (MODE == TPT_APPLY && a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot);
 }
 
 }  // namespace hdg

@@ -1,7 +1,9 @@
 """GPU parity of the condensed operator K (hdg_apply) against the CPU oracle.
 
 The FP64 apply must match the oracle's dense-condensed global apply within
-1e-12 relative (max-norm); the FP32 apply within 1e-5.  Meshes span several
+1e-12 relative (max-norm); the FP32 apply within 1e-5; the BF16-stored apply
+(transformed basis) within 2^-6 of the oracle applied to the same
+BF16-representable input.  Meshes span several
 CTAs with ragged tails, stretched grids, mixed Dirichlet/Neumann sides,
 single-element directions, and degrees 1..16.  At the full sizes of the
 16^3 stretched p = 8 and 32^3 uniform p = 8 workloads, sampled outputs are
@@ -184,3 +186,25 @@ def test_autotune_keeps_results_and_cache(tmp_path):
     assert h2.autotune("fp32", 1, 2.0, cache=cache) == (seg, slots, us)   # served from the cache
     with pytest.raises(Exception):
         h2.set_slots_per_cta(10000)
+
+
+@pytest.mark.parametrize("ne,bc,p,stretched", [((5, 4, 3), (0, 1, 0, 0, 1, 0), 5, True),
+                                               ((16, 16, 16), (0,) * 6, 8, True)])
+def test_apply_bf16_storage(ne, bc, p, stretched):
+    # BF16 trace storage, FP32 arithmetic, transformed basis.  Reference: the
+    # FP64 transformed apply of the same (BF16-representable) input; the
+    # output rounds each of a face's two contributions to BF16 (relative
+    # 2^-9 each), so 2^-6 of the largest value leaves room for cancellation
+    from paper_2007_11891_gb300 import HDG
+    h = HDG(ne, _grid(ne, stretched, 6), bc, p, 25.0)
+    x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 21), device="cuda").to(torch.bfloat16)
+    y = h.apply(x, 1.5, basis="transformed")
+    assert y.dtype == torch.bfloat16
+    ref = h.apply(x.double(), 1.5, basis="transformed")
+    err = (y.double() - ref).abs().max().item()
+    assert err <= 2.0 ** -6 * ref.abs().max().item()
+    assert torch.equal(h.apply(x, 1.5, basis="transformed"), y)   # bitwise repeatable
+    h.set_x1_segment(1)
+    assert torch.equal(h.apply(x, 1.5, basis="transformed"), y)   # independent of the runs
+    with pytest.raises(Exception):
+        h.apply(x, 1.5, basis="nodal")
