@@ -427,13 +427,17 @@ def run_sweep(args):
 def run_probe(args):
     """Short, untimed workload for ncu captures: set-up, one warm-up, then
     `--steps` repetitions of the probed step (mixed solve, or one operator
-    application in FP32/FP64 in the transformed basis) on the bench workload."""
+    application in FP32/FP64 in the transformed basis) on the bench workload.
+    With --eager the solve launches its kernels one by one (the same kernels
+    as inside the CUDA graph)."""
     import torch
     from paper_2007_11891_gb300 import HDG
     torch.cuda.set_device(0)
     cfg = hdg_inputs.WORKLOADS[args.workload]
     ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"] or 1.0
     h = HDG(ne, hdg_inputs.grid_lines(ne, cfg["stretched"]), (0,) * 6, p, hdg_inputs.TAU_HAT)
+    if args.eager:
+        h.profile(True)   # per-launch events; keeps the solver off CUDA graphs
     if args.probe == "solve":
         f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11890), device="cuda")
         step = lambda: h.solve(f, lam, tol=1e-10, inner="fp32", return_u=True)
@@ -459,6 +463,9 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="extra measurements instead of the bench line")
     ap.add_argument("--probe", choices=["solve", "apply32", "apply64"], help="untimed workload for ncu")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(hdg_inputs.WORKLOADS))
+    ap.add_argument("--eager", action="store_true",
+                    help="probe: launch the CG loop kernel by kernel (no CUDA graphs), so that profilers that "
+                         "cannot enter conditional graph nodes see every launch")
     args = ap.parse_args()
     if args.probe:
         run_probe(args)

@@ -11,6 +11,13 @@ namespace hdg {
 
 constexpr int kMaxNDev = 17;
 
+// Dynamic shared memory above which a kernel's limit is raised explicitly
+// (cudaFuncAttributeMaxDynamicSharedMemorySize).  The default limit of 48 KB
+// covers dynamic plus static shared memory, and the operator kernels hold a
+// little static shared memory for their reductions, so the opt-in starts
+// well below 48 KB.
+constexpr size_t kSmemOptIn = 40 * 1024;
+
 // Cartesian mesh in the library's face-wise layout (see include/hdg.h).
 struct MeshDev {
   int ne[3];          // elements per direction
@@ -27,8 +34,9 @@ struct CgScalars {
   double rr;        // gamma = r . u of the current iterate (u = W r)
   double rr_old;    // gamma of the previous iterate
   double rr_stop;   // stop when rr <= rr_stop
-  double alpha, beta;   // of the last step
-  int it, max_it;
+  double alpha, beta;   // step length and direction update of the current step
+  int it, max_it;   // completed update steps, cap
+  int ops;          // operator launches whose scalars are done
   int done;         // 1: stop (converged, iteration cap or breakdown)
   int status;       // 0 ok / converged, 5 not converged, 6 breakdown
 };

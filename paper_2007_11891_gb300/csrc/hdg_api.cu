@@ -13,10 +13,23 @@
 namespace {
 
 thread_local std::string g_last_error;
+// a (non-sticky) CUDA error that was already pending when the current entry
+// point started: cleared at entry so that it is not blamed on this call's
+// own launches, and quoted if this call fails
+thread_local std::string g_pending;
 
 hdg_status fail(hdg_status s, const std::string& msg) {
-  g_last_error = msg;
+  g_last_error = g_pending.empty() ? msg : msg + " [CUDA error pending before this call: " + g_pending + "]";
   return s;
+}
+
+// Entry-point prologue: clear the message of the previous call and take any
+// pending CUDA error out of the runtime's error slot.
+void begin_call() {
+  g_last_error.clear();
+  g_pending.clear();
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) g_pending = cudaGetErrorString(e);
 }
 
 #define HDG_CUDA(...)                                                                   \
@@ -65,6 +78,7 @@ struct hdg_ctx {
   // workspaces
   DevBuf ws[24];
   DevBuf partials, counters, cgs, flags, scal;
+  DevBuf step_partials;   // per-block gamma partials of the CG update step
   int red_blocks = 0;
   // measurement: launch count and optional event pairs per kernel class
   bool prof_on = false;
@@ -260,7 +274,13 @@ hdg_status tpt_apply(hdg_ctx* c, int nrhs, const T* dinv, const ST* x, ST* y, cu
   a.skip = skip;
   a.hook = hook;
   Timed t(c, sizeof(T) == 8 ? K_OP64 : K_OP32, s);
-  HDG_CUDA(hdg::launch_tpt<T, ST>(hdg::TPT_APPLY, c->n, a, nrhs, s));
+  const cudaError_t e = hdg::launch_tpt<T, ST>(hdg::TPT_APPLY, c->n, a, nrhs, s);
+  if (e != cudaSuccess)
+    return fail(HDG_ERR_CUDA, std::string("operator launch (") + (sizeof(T) == 8 ? "FP64" : "FP32") +
+                                  ", n=" + std::to_string(c->n) + ", slots=" + std::to_string(a.ppb) +
+                                  ", seg=" + std::to_string(a.seg) + "x" + std::to_string(a.nseg) +
+                                  ", run=" + std::to_string(a.chunk) + ", grid cap=" + std::to_string(a.max_grid) +
+                                  ", nrhs=" + std::to_string(nrhs) + "): " + cudaGetErrorString(e));
   return HDG_OK;
 }
 
@@ -278,11 +298,12 @@ int reduction_blocks(long long len) {
 }
 
 hdg_status ensure_reductions(hdg_ctx* c, int nrhs) {
-  c->red_blocks = 152 * 8;   // upper bound on blocks of any reducing vector launch
+  c->red_blocks = std::max(c->sms, 152) * 8;   // upper bound on blocks of any reducing vector launch (8 x 256 threads per SM)
   // the operator grid is largest with one element per CTA (one slot, runs of one)
   const long long tpt_b = c->nelem;
   const long long pb = std::max<long long>(c->red_blocks, tpt_b);
   HDG_TRY(ensure(c->partials, sizeof(double) * (size_t)nrhs * pb));
+  HDG_TRY(ensure(c->step_partials, sizeof(double) * (size_t)nrhs * c->red_blocks));
   const bool fresh = c->counters.bytes < sizeof(unsigned int) * (size_t)nrhs;
   HDG_TRY(ensure(c->counters, sizeof(unsigned int) * (size_t)nrhs));
   if (fresh) HDG_CUDA(cudaMemset(c->counters.p, 0, c->counters.bytes));
@@ -356,15 +377,16 @@ hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, 
   int* flags = static_cast<int*>(c->flags.p);
   hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
   double* uw = static_cast<double*>(c->scal.p) + nrhs;
-  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), uw, cg};
+  const int vb = hdg::cg_step_blocks<T>(T_);
+  double* gp = static_cast<double*>(c->step_partials.p);
+  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), uw, cg, flags,
+                   gp, vb};
   T* u = wsp<T>(c, W_U);
   T* sv = wsp<T>(c, W_S);
-  const int vb = hdg::cg_step_blocks<T>(T_);
   for (int k = 0; k < count; ++k) {
     HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, u, q, s, flags, hook, true)));
     Timed t_(c, K_VEC, s);
-    HDG_CUDA(hdg::launch_cg_step<T>(cg, flags, d, r, u, q, p, sv, w, T_, nrhs, static_cast<double*>(c->partials.p),
-                                    static_cast<unsigned int*>(c->counters.p), vb, s));
+    HDG_CUDA(hdg::launch_cg_step<T>(cg, flags, d, r, u, q, p, sv, w, T_, nrhs, gp, vb, s));
   }
   return HDG_OK;
 }
@@ -381,7 +403,7 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
                                 (uintptr_t)c->ws[W_U].p, (uintptr_t)c->ws[W_S].p, (uintptr_t)w, (uintptr_t)r,
                                 (uintptr_t)d, (uintptr_t)p, (uintptr_t)q, (uintptr_t)c->flags.p,
                                 (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p, (uintptr_t)c->partials.p,
-                                (uintptr_t)c->counters.p, (uintptr_t)count, (uintptr_t)c->seg_override,
+                                (uintptr_t)c->step_partials.p, (uintptr_t)c->counters.p, (uintptr_t)count, (uintptr_t)c->seg_override,
                                 (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode};
   GraphEntry* ge = nullptr;
   for (GraphEntry& g : c->graphs)
@@ -437,7 +459,8 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
                                 (uintptr_t)c->ws[W_U].p, (uintptr_t)c->ws[W_S].p,
                                 (uintptr_t)w, (uintptr_t)r, (uintptr_t)d, (uintptr_t)p, (uintptr_t)q,
                                 (uintptr_t)c->flags.p, (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p,
-                                (uintptr_t)c->partials.p, (uintptr_t)c->counters.p, (uintptr_t)c->loopctl.p,
+                                (uintptr_t)c->partials.p, (uintptr_t)c->step_partials.p,
+                                (uintptr_t)c->counters.p, (uintptr_t)c->loopctl.p,
                                 (uintptr_t)c->seg_override, (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode};
   GraphEntry* ge = nullptr;
   for (GraphEntry& g : c->graphs)
@@ -786,7 +809,7 @@ hdg_status hdg_set_slots_per_cta(hdg_ctx* c, int slots) {
 
 hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precision prec, int* h_best_segment,
                         int* h_best_slots, double* h_best_us, void* stream) {
-  g_last_error.clear();
+  begin_call();
   if (!c || nrhs < 1 || prec == HDG_BF16) return fail(HDG_ERR_INVALID_ARG, "NULL context, nrhs < 1 or BF16");
   HDG_TRY(check_lambda(c, nrhs, h_lambda));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -912,7 +935,7 @@ const char* hdg_status_string(hdg_status s) {
 }
 
 hdg_status hdg_setup(const hdg_mesh* mesh, int p, const hdg_options* opts, hdg_ctx** out) {
-  g_last_error.clear();
+  begin_call();
   if (!mesh || !out) return fail(HDG_ERR_INVALID_ARG, "mesh and out must not be NULL");
   *out = nullptr;
   if (p < 1 || p > 16) return fail(HDG_ERR_UNSUPPORTED, "degree p must be in 1..16");
@@ -1049,7 +1072,8 @@ void hdg_destroy(hdg_ctx* c) {
   cudaFree(c->d_metric32);
   cudaFree(c->d_Lambda);
   cudaFree(c->d_widths);
-  for (DevBuf* b : {&c->dinv64, &c->dinv32, &c->lam_dev64, &c->lam_dev32, &c->partials, &c->counters, &c->cgs,
+  for (DevBuf* b : {&c->dinv64, &c->dinv32, &c->lam_dev64, &c->lam_dev32, &c->partials, &c->step_partials,
+                    &c->counters, &c->cgs,
                     &c->flags, &c->scal})
     if (b->p) cudaFree(b->p);
   for (DevBuf& b : c->ws)
@@ -1075,7 +1099,7 @@ hdg_status hdg_get_nodes(const hdg_ctx* c, double* h_nodes) {
 
 hdg_status hdg_apply(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precision prec, hdg_basis basis,
                      const void* d_x, void* d_y, void* stream) {
-  g_last_error.clear();
+  begin_call();
   if (!c || !d_x || !d_y || nrhs < 1) return fail(HDG_ERR_INVALID_ARG, "NULL pointer or nrhs < 1");
   HDG_TRY(check_lambda(c, nrhs, h_lambda));
   if (basis != HDG_BASIS_NODAL && basis != HDG_BASIS_TRANSFORMED) return fail(HDG_ERR_INVALID_ARG, "bad basis");
@@ -1125,7 +1149,7 @@ hdg_status hdg_apply(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precision
 hdg_status hdg_solve(hdg_ctx* c, int nrhs, const double* h_lambda, const double* d_f, const double* d_bdry,
                      const double* d_x0, double* d_trace, double* d_u, const hdg_solve_opts* opts,
                      hdg_solve_info* h_info, void* stream) {
-  g_last_error.clear();
+  begin_call();
   if (!c || !d_f || !d_trace || nrhs < 1) return fail(HDG_ERR_INVALID_ARG, "NULL pointer or nrhs < 1");
   HDG_TRY(check_lambda(c, nrhs, h_lambda));
   return solve_impl(c, nrhs, h_lambda, d_f, false, d_bdry, d_x0, d_trace, d_u, opts, h_info,
@@ -1135,7 +1159,7 @@ hdg_status hdg_solve(hdg_ctx* c, int nrhs, const double* h_lambda, const double*
 hdg_status hdg_solve_adjoint(hdg_ctx* c, int nrhs, const double* h_lambda, const double* d_u,
                              const double* d_grad_u, double* d_grad_f, double* d_grad_lambda,
                              const hdg_solve_opts* opts, hdg_solve_info* h_info, void* stream) {
-  g_last_error.clear();
+  begin_call();
   if (!c || !d_u || !d_grad_u || !d_grad_f || !d_grad_lambda || nrhs < 1)
     return fail(HDG_ERR_INVALID_ARG, "NULL pointer or nrhs < 1");
   HDG_TRY(check_lambda(c, nrhs, h_lambda));

@@ -76,16 +76,16 @@ cudaError_t launch_pc_invert(const double* diag, double* w64, float* w32, long l
 cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, const double* tol, int max_it,
                            int nrhs, cudaStream_t s);
 // One step of the single-reduction CG (Chronopoulos-Gear) after the operator
-// launch w = K u whose hook stored the step scalars (cg_scalars): updates p,
-// s, x, r, u = W r (W = I if null), zeroes w, and the last block stores
-// gamma = r . u, the iteration count and flags[r] (no effect once done).
-// `blocks` from cg_step_blocks (one resident wave).
+// launch w = K u whose hook produced the step scalars (cg_scalars): updates
+// p, s, x, r, u = W r (W = I if null), zeroes w, and leaves the per-block
+// partial sums of gamma = r . u in partials[r][block] for the next operator
+// launch.  Skips right-hand sides with flags[r] set.  `blocks` from
+// cg_step_blocks (one resident wave).
 template <typename T>
 int cg_step_blocks(long long len);
 template <typename T>
-cudaError_t launch_cg_step(CgScalars* cg, int* flags, T* x, T* r, T* u, T* w, T* p, T* sv, const T* W,
-                           long long len, int nrhs, double* partials, unsigned int* counter, int blocks,
-                           cudaStream_t s);
+cudaError_t launch_cg_step(const CgScalars* cg, const int* flags, T* x, T* r, T* u, T* w, T* p, T* sv,
+                           const T* W, long long len, int nrhs, double* partials, int blocks, cudaStream_t s);
 // p = W r + beta p (skips finished right-hand sides)
 template <typename T>
 cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w, long long len, int nrhs,

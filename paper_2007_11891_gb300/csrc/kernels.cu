@@ -430,6 +430,7 @@ __global__ void cg_init_kernel(CgScalars* cg, int* flags, const double* rr, cons
   c.alpha = 0.0;
   c.beta = 0.0;
   c.it = 0;
+  c.ops = 0;
   c.max_it = max_it;
   c.status = 0;
   c.done = (flags[r] != 0) || !(c.rr > 0.0) || max_it <= 0;
@@ -440,22 +441,24 @@ __global__ void cg_init_kernel(CgScalars* cg, int* flags, const double* rr, cons
 
 // One iteration of the single-reduction preconditioned CG of Chronopoulos
 // and Gear, after the operator launch w_i = K u_i, whose last block already
-// turned delta_i = u_i . w_i into the step scalars (cg_scalars):
+// produced the step scalars alpha_i, beta_i (cg_scalars):
 //   p_i = u_i + beta_i p_{i-1},  s_i = w_i + beta_i s_{i-1}   (s_i = K p_i)
 //   x_{i+1} = x_i + alpha_i p_i,  r_{i+1} = r_i - alpha_i s_i
-//   u_{i+1} = W r_{i+1},  gamma_{i+1} = r_{i+1} . u_{i+1}
+//   u_{i+1} = W r_{i+1},  gamma_{i+1} = r_{i+1} . u_{i+1}.
 // In exact arithmetic these are the iterates of the standard preconditioned
 // CG; the two inner products of an iteration meet in one reduction phase, so
-// an iteration is two kernels (operator, this update).  w is zeroed for the
-// next operator launch, which accumulates into it.  Every thread issues all
-// loads of its entries before it reads the scalars (no barrier before the
-// streams start); one resident wave of blocks covers the vectors.
+// an iteration is two kernels (operator, this update).  gamma_{i+1} is left
+// as one partial sum per block in `partials`: the next operator launch's
+// last block adds them up (in a fixed order) with its own inner product, so
+// this kernel has no grid-wide reduction tail.  w is zeroed for the next
+// operator launch, which accumulates into it.  Every thread issues all loads
+// of its entries before it reads the scalars; one resident wave of blocks
+// covers the vectors.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) cg_step_kernel(CgScalars* cg, int* flags, T* __restrict__ x,
-                                                        T* __restrict__ rvec, T* __restrict__ u,
-                                                        T* __restrict__ wv, T* __restrict__ p,
-                                                        T* __restrict__ sv, const T* __restrict__ W,
-                                                        long long len, double* partials, unsigned int* counter) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+    cg_step_kernel(const CgScalars* cg, const int* flags, T* __restrict__ x, T* __restrict__ rvec,
+                   T* __restrict__ u, T* __restrict__ wv, T* __restrict__ p, T* __restrict__ sv,
+                   const T* __restrict__ W, long long len, double* partials) {
   const int r = blockIdx.y;
   if (flags[r]) return;
   const long long o = r * len;
@@ -508,24 +511,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) cg_step_kernel(Cg
     }
   }
   const double sblk = block_sum(static_cast<double>(acc));
-  if (finish_partial(sblk, partials, counter, r)) {
-    const double gnew = sum_partials(partials, r);
-    if (threadIdx.x != 0) return;
-    counter[r] = 0u;
-    CgScalars c = cg[r];
-    c.it += 1;
-    if (c.status == 6 || !(gnew == gnew)) {
-      c.status = 6;
-      c.done = 1;
-    } else {
-      c.rr_old = c.rr;
-      c.rr = gnew;
-      if (gnew <= c.rr_stop) c.done = 1;
-      else if (c.it >= c.max_it) { c.done = 1; c.status = 5; }
-    }
-    cg[r] = c;
-    flags[r] = c.done;
-  }
+  if (threadIdx.x == 0) partials[(long long)r * gridDim.x + blockIdx.x] = sblk;
 }
 
 template <typename T>
@@ -599,7 +585,7 @@ cudaError_t vt_launch(const double* x, double* y, long long nelem, int nrhs, lon
   const int epb = (256 / (N * N)) > 0 ? 256 / (N * N) : 1;
   const int threads = (epb * N * N + 31) / 32 * 32;
   const size_t smem = (size_t)epb * 2 * N * N * N * sizeof(double);
-  if (smem > 48 * 1024)
+  if (smem > kSmemOptIn)
     cudaFuncSetAttribute(volume_transform_kernel<N, PAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   dim3 grid((unsigned)((nelem + epb - 1) / epb), nrhs);
   if (nelem <= 0) return cudaSuccess;
@@ -756,21 +742,19 @@ int cg_step_blocks(long long len) {
 }
 
 template <typename T>
-cudaError_t launch_cg_step(CgScalars* cg, int* flags, T* x, T* r, T* u, T* w, T* p, T* sv, const T* W,
-                           long long len, int nrhs, double* partials, unsigned int* counter, int blocks,
-                           cudaStream_t s) {
+cudaError_t launch_cg_step(const CgScalars* cg, const int* flags, T* x, T* r, T* u, T* w, T* p, T* sv,
+                           const T* W, long long len, int nrhs, double* partials, int blocks, cudaStream_t s) {
   dim3 grid(blocks, nrhs);
-  cg_step_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, x, r, u, w, p, sv, W, len, partials, counter);
+  cg_step_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, x, r, u, w, p, sv, W, len, partials);
   return cudaGetLastError();
 }
 template int cg_step_blocks<double>(long long);
 template int cg_step_blocks<float>(long long);
-template cudaError_t launch_cg_step<double>(CgScalars*, int*, double*, double*, double*, double*, double*,
-                                            double*, const double*, long long, int, double*, unsigned int*,
-                                            int, cudaStream_t);
-template cudaError_t launch_cg_step<float>(CgScalars*, int*, float*, float*, float*, float*, float*, float*,
-                                           const float*, long long, int, double*, unsigned int*, int,
-                                           cudaStream_t);
+template cudaError_t launch_cg_step<double>(const CgScalars*, const int*, double*, double*, double*, double*,
+                                            double*, double*, const double*, long long, int, double*, int,
+                                            cudaStream_t);
+template cudaError_t launch_cg_step<float>(const CgScalars*, const int*, float*, float*, float*, float*, float*,
+                                           float*, const float*, long long, int, double*, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w, long long len, int nrhs,

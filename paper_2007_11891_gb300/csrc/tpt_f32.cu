@@ -13,7 +13,7 @@ int fast_occupancy(int ppb) {
   if (cached[key] > 0) return cached[key];
   const int threads = tpt_threads(N, ppb);
   const size_t smem = (size_t)ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
-  if (smem > 48 * 1024)
+  if (smem > kSmemOptIn)
     cudaFuncSetAttribute(tpt_fast_kernel<N, DZC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpt_fast_kernel<N, DZC>, threads, smem) !=
@@ -34,7 +34,7 @@ cudaError_t fast_launch(const TptArgs<float, ST>& a, int nrhs, cudaStream_t s) {
   const int threads = tpt_threads(N, a.ppb);
   const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
   if (threads > fast_max_threads(N)) return cudaErrorInvalidConfiguration;
-  if (smem > 48 * 1024) {
+  if (smem > kSmemOptIn) {
     cudaError_t e = cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -46,27 +46,51 @@ struct CgHook {
   double* partials;        // [nrhs][gridDim.x]
   unsigned int* counter;   // [nrhs], zero between launches
   double* pq;              // [nrhs] result: x^T K x
-  CgScalars* cg;           // non-null: also the step scalars of the CG (cg_scalars)
+  // inside the CG loop: the scalars of the single-reduction CG (cg_scalars),
+  // with the per-block partial sums of gamma left by the previous update step
+  CgScalars* cg;
+  int* flags;
+  const double* step_partials;   // [nrhs][step_blocks]
+  int step_blocks;
 };
 
-// Step scalars of the single-reduction CG (Chronopoulos-Gear) once
-// delta_i = u_i^T K u_i is known, with gamma_i = rr, gamma_{i-1} = rr_old and
-// alpha_{i-1} = alpha of the previous step:
-//   beta_i = gamma_i / gamma_{i-1} (0 in the first step),
-//   alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1}).
-// A non-positive or non-finite denominator is a breakdown: status 6 and
-// zero steps (the update kernel then stops this right-hand side).
-__device__ __forceinline__ void cg_scalars(CgScalars* cgp, double delta) {
+// Scalars of the single-reduction CG (Chronopoulos-Gear) at the end of the
+// operator launch of iteration i, once delta_i = u_i^T K u_i is known.
+// For i > 0 the previous update step left gamma_i = r_i . u_i as per-block
+// partial sums (summed by the caller, so that the update kernel needs no
+// reduction of its own): beta_i = gamma_i / gamma_{i-1}, and the convergence
+// test gamma_i <= rr_stop or the iteration cap may stop this right-hand side
+// here.  Then alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1})
+// (delta_0 alone for i = 0).  A non-positive or non-finite denominator is a
+// breakdown (status 6).  flags[r] mirrors done.
+__device__ __forceinline__ void cg_scalars(CgScalars* cgp, int* flag, double delta, double gamma_new) {
   CgScalars c = *cgp;
   if (c.done) return;
-  const bool first = c.it == 0;
-  const double gam = c.rr;
-  const double beta = first ? 0.0 : gam / c.rr_old;
-  const double den = first ? delta : delta - beta * gam / c.alpha;
-  const bool bad = !(den > 0.0) || !(den <= 1.79e308) || !(gam == gam);
-  cgp->alpha = bad ? 0.0 : gam / den;
-  cgp->beta = bad ? 0.0 : beta;
-  if (bad) cgp->status = 6;
+  if (c.ops > 0) {
+    c.it = c.ops;
+    if (!(gamma_new == gamma_new)) {
+      c.status = 6;
+      c.done = 1;
+    } else {
+      c.beta = gamma_new / c.rr;
+      c.rr_old = c.rr;
+      c.rr = gamma_new;
+      if (gamma_new <= c.rr_stop) c.done = 1;
+      else if (c.it >= c.max_it) { c.done = 1; c.status = 5; }
+    }
+  }
+  if (!c.done) {
+    const double den = c.ops == 0 ? delta : delta - c.beta * c.rr / c.alpha;
+    if (!(den > 0.0) || !(den <= 1.79e308) || !(c.rr == c.rr)) {
+      c.status = 6;
+      c.done = 1;
+    } else {
+      c.alpha = c.rr / den;
+      c.ops += 1;
+    }
+  }
+  *cgp = c;
+  *flag = c.done;
 }
 
 template <typename T>
@@ -105,12 +129,28 @@ __device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, double 
     __syncthreads();
     if ((tid & 31) == 0) wsum[tid >> 5] = s;
     __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
+    double t = 0.0;
+    if (tid == 0)
       for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += wsum[w];
+    if (hook.cg) {
+      // gamma from the previous update step's partials (fixed order)
+      double g = 0.0;
+      if (hook.cg[rhs].ops > 0) {
+        const double* gp = hook.step_partials + (long long)rhs * hook.step_blocks;
+        for (int b = tid; b < hook.step_blocks; b += blockDim.x) g += gp[b];
+        g = warp_sum(g);
+        __syncthreads();
+        if ((tid & 31) == 0) wsum[tid >> 5] = g;
+        __syncthreads();
+        g = 0.0;
+        if (tid == 0)
+          for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) g += wsum[w];
+      }
+      if (tid == 0) cg_scalars(hook.cg + rhs, hook.flags + rhs, t, g);
+    }
+    if (tid == 0) {
       hook.pq[rhs] = t;
       hook.counter[rhs] = 0u;
-      if (hook.cg) cg_scalars(hook.cg + rhs, t);
     }
   }
 }

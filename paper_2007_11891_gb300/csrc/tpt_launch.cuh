@@ -12,7 +12,7 @@ cudaError_t tpt_launch_one(const TptArgs<T, ST>& a, int nrhs, cudaStream_t s) {
   const int threads = tpt_threads(N, a.ppb);
   const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<T, N>() * sizeof(T);
   if (threads > 320) return cudaErrorInvalidConfiguration;
-  if (smem > 48 * 1024) {
+  if (smem > kSmemOptIn) {
     cudaError_t e = cudaFuncSetAttribute(tpt_kernel<T, ST, N, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -33,7 +33,7 @@ int tpt_occupancy_one(int ppb) {
   if (cached[key] > 0) return cached[key];
   const int threads = tpt_threads(N, ppb);
   const size_t smem = (size_t)ppb * tpt_smem_per_pencil<T, N>() * sizeof(T);
-  if (smem > 48 * 1024)
+  if (smem > kSmemOptIn)
     cudaFuncSetAttribute(tpt_kernel<T, ST, N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int nb = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpt_kernel<T, ST, N, MODE>, threads, smem) != cudaSuccess ||
