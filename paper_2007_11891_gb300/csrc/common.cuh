@@ -116,6 +116,15 @@ __device__ __forceinline__ void store_from<__nv_bfloat16, float>(__nv_bfloat16* 
   *p = __float2bfloat16_rn(v);
 }
 
+// Programmatic dependent launch (sm_90+): a kernel launched with
+// programmatic stream serialization may start while the previous kernel in
+// the stream is still finishing; grid_dep_wait() blocks until that kernel
+// has completed and its memory operations are visible (a no-op without such
+// a dependency), and grid_dep_launch() lets the next kernel's blocks be
+// scheduled once every block of this grid has signalled or exited.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // y += v with a single global reduction (L2 atomic).  Exactly two adds reach
 // an interior face value that starts at zero: 0 + a + b == 0 + b + a in IEEE
 // arithmetic, so the result does not depend on their order.

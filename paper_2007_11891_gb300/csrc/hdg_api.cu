@@ -98,6 +98,9 @@ struct hdg_ctx {
   bool capturing = false;
   int graphs_enabled = 1;
   int loop_graphs_enabled = 1;
+  // programmatic dependent launch between the CG loop kernels (dropped if a
+  // graph with it cannot be built)
+  int pdl = 1;
   DevBuf loopctl;   // device loop-trip counter of the CG loop graph
   int seg_override = 0;   // x1 segment length; 0 = automatic
   int ppb_override = 0;   // slots per CTA; 0 = automatic
@@ -265,7 +268,8 @@ hdg_status zero_for_tpt(const hdg_ctx* c, ST* y, int nrhs, int nseg, cudaStream_
 // y = K-hat x; `zeroed` says the caller already zeroed y (the CG update does)
 template <typename T, typename ST>
 hdg_status tpt_apply(hdg_ctx* c, int nrhs, const T* dinv, const ST* x, ST* y, cudaStream_t s,
-                     const int* skip = nullptr, hdg::CgHook hook = hdg::CgHook{}, bool zeroed = false) {
+                     const int* skip = nullptr, hdg::CgHook hook = hdg::CgHook{}, bool zeroed = false,
+                     bool pdl = false) {
   hdg::TptArgs<T, ST> a = base_args<T, ST>(c, dinv, nrhs);
   // the FP32 kernel's runs may split any x1-pencil: zero the whole output
   if (!zeroed) HDG_TRY(zero_for_tpt<ST>(c, y, nrhs, sizeof(T) == 4 ? 2 : a.nseg, s));
@@ -273,6 +277,7 @@ hdg_status tpt_apply(hdg_ctx* c, int nrhs, const T* dinv, const ST* x, ST* y, cu
   a.y = y;
   a.skip = skip;
   a.hook = hook;
+  a.pdl = pdl ? 1 : 0;
   Timed t(c, sizeof(T) == 8 ? K_OP64 : K_OP32, s);
   const cudaError_t e = hdg::launch_tpt<T, ST>(hdg::TPT_APPLY, c->n, a, nrhs, s);
   if (e != cudaSuccess)
@@ -383,10 +388,15 @@ hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, 
                    gp, vb};
   T* u = wsp<T>(c, W_U);
   T* sv = wsp<T>(c, W_S);
+  // programmatic dependent launch: each loop kernel may be scheduled while
+  // the previous one drains (the FP32 operator kernel and the update kernel
+  // wait for their predecessor before reading anything it wrote; the FP64
+  // operator kernel is launched normally)
+  const bool pdl = c->pdl != 0;
   for (int k = 0; k < count; ++k) {
-    HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, u, q, s, flags, hook, true)));
+    HDG_TRY((tpt_apply<T, T>(c, nrhs, dinv, u, q, s, flags, hook, true, pdl && sizeof(T) == 4)));
     Timed t_(c, K_VEC, s);
-    HDG_CUDA(hdg::launch_cg_step<T>(cg, flags, d, r, u, q, p, sv, w, T_, nrhs, gp, vb, s));
+    HDG_CUDA(hdg::launch_cg_step<T>(cg, flags, d, r, u, q, p, sv, w, T_, nrhs, gp, vb, pdl, s));
   }
   return HDG_OK;
 }
@@ -403,7 +413,8 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
                                 (uintptr_t)c->ws[W_U].p, (uintptr_t)c->ws[W_S].p, (uintptr_t)w, (uintptr_t)r,
                                 (uintptr_t)d, (uintptr_t)p, (uintptr_t)q, (uintptr_t)c->flags.p,
                                 (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p, (uintptr_t)c->partials.p,
-                                (uintptr_t)c->step_partials.p, (uintptr_t)c->counters.p, (uintptr_t)count, (uintptr_t)c->seg_override,
+                                (uintptr_t)c->step_partials.p, (uintptr_t)c->counters.p, (uintptr_t)count,
+                                (uintptr_t)c->pdl, (uintptr_t)c->seg_override,
                                 (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode};
   GraphEntry* ge = nullptr;
   for (GraphEntry& g : c->graphs)
@@ -461,7 +472,8 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
                                 (uintptr_t)c->flags.p, (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p,
                                 (uintptr_t)c->partials.p, (uintptr_t)c->step_partials.p,
                                 (uintptr_t)c->counters.p, (uintptr_t)c->loopctl.p,
-                                (uintptr_t)c->seg_override, (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode};
+                                (uintptr_t)c->seg_override, (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode,
+                                (uintptr_t)c->pdl};
   GraphEntry* ge = nullptr;
   for (GraphEntry& g : c->graphs)
     if (g.key == key) ge = &g;
@@ -469,9 +481,14 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
   if (!ge) {
     auto give_up = [&](cudaGraph_t g) {
       if (g) cudaGraphDestroy(g);
-      c->loop_graphs_enabled = 0;
       cudaGetLastError();
       g_last_error.clear();
+      if (c->pdl) {
+        // try once more without programmatic dependent launch
+        c->pdl = 0;
+        return cg_loop_graph<T>(c, nrhs, dinv, w, r, d, p, q, s, st);
+      }
+      c->loop_graphs_enabled = 0;
       return false;
     };
     if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)

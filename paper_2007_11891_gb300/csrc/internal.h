@@ -80,12 +80,14 @@ cudaError_t launch_cg_init(CgScalars* cg, int* flags, const double* rr, const do
 // p, s, x, r, u = W r (W = I if null), zeroes w, and leaves the per-block
 // partial sums of gamma = r . u in partials[r][block] for the next operator
 // launch.  Skips right-hand sides with flags[r] set.  `blocks` from
-// cg_step_blocks (one resident wave).
+// cg_step_blocks (one resident wave).  pdl: programmatic dependent launch on
+// the operator launch before it.
 template <typename T>
 int cg_step_blocks(long long len);
 template <typename T>
 cudaError_t launch_cg_step(const CgScalars* cg, const int* flags, T* x, T* r, T* u, T* w, T* p, T* sv,
-                           const T* W, long long len, int nrhs, double* partials, int blocks, cudaStream_t s);
+                           const T* W, long long len, int nrhs, double* partials, int blocks, bool pdl,
+                           cudaStream_t s);
 // p = W r + beta p (skips finished right-hand sides)
 template <typename T>
 cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w, long long len, int nrhs,

@@ -460,6 +460,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
                    T* __restrict__ u, T* __restrict__ wv, T* __restrict__ p, T* __restrict__ sv,
                    const T* __restrict__ W, long long len, double* partials) {
   const int r = blockIdx.y;
+  grid_dep_wait();     // the operator launch before this one wrote w, the scalars and flags
+  grid_dep_launch();   // the next operator launch may queue its blocks behind this wave
   if (flags[r]) return;
   const long long o = r * len;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -743,18 +745,32 @@ int cg_step_blocks(long long len) {
 
 template <typename T>
 cudaError_t launch_cg_step(const CgScalars* cg, const int* flags, T* x, T* r, T* u, T* w, T* p, T* sv,
-                           const T* W, long long len, int nrhs, double* partials, int blocks, cudaStream_t s) {
+                           const T* W, long long len, int nrhs, double* partials, int blocks, bool pdl,
+                           cudaStream_t s) {
   dim3 grid(blocks, nrhs);
+  if (pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kVecThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, cg_step_kernel<T>, cg, flags, x, r, u, w, p, sv, W, len, partials);
+  }
   cg_step_kernel<T><<<grid, kVecThreads, 0, s>>>(cg, flags, x, r, u, w, p, sv, W, len, partials);
   return cudaGetLastError();
 }
 template int cg_step_blocks<double>(long long);
 template int cg_step_blocks<float>(long long);
 template cudaError_t launch_cg_step<double>(const CgScalars*, const int*, double*, double*, double*, double*,
-                                            double*, double*, const double*, long long, int, double*, int,
+                                            double*, double*, const double*, long long, int, double*, int, bool,
                                             cudaStream_t);
 template cudaError_t launch_cg_step<float>(const CgScalars*, const int*, float*, float*, float*, float*, float*,
-                                           float*, const float*, long long, int, double*, int, cudaStream_t);
+                                           float*, const float*, long long, int, double*, int, bool, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_cg_pupdate(const CgScalars* cg, T* p, const T* r, const T* w, long long len, int nrhs,

@@ -42,6 +42,19 @@ cudaError_t fast_launch(const TptArgs<float, ST>& a, int nrhs, cudaStream_t s) {
   // one run of `chunk` elements per slot: every element is covered exactly once
   const long long blocks = (nelem + (long long)a.chunk * a.ppb - 1) / ((long long)a.chunk * a.ppb);
   dim3 grid((unsigned)blocks, (unsigned)nrhs);
+  if (a.pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tpt_fast_kernel<N, DZC, ST>, a);
+  }
   tpt_fast_kernel<N, DZC, ST><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }

@@ -49,6 +49,8 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   float* sm = reinterpret_cast<float*>(smem_raw);
 
   const int rhs = blockIdx.y;
+  // everything below reads what the previous kernel in the stream wrote
+  grid_dep_wait();
   if (a.skip && a.skip[rhs]) return;   // uniform per block
 
   const int tid = threadIdx.x;
@@ -248,6 +250,7 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
     x2l = n2l; x2h = n2h; x3l = n3l; x3h = n3h;
   }
 
+  grid_dep_launch();   // the next kernel's blocks may take this block's place
   if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot);
 }
 

@@ -181,6 +181,7 @@ struct TptArgs {
   int max_grid;                 // CTAs launched (grid-stride over slot groups); 0 = one per group
   const int* skip;              // per rhs: nonzero -> do nothing (converged), or null
   CgHook hook;                  // partials == null: no dot
+  int pdl;                      // host: launch with programmatic stream serialization
 };
 
 // Shared memory per pencil slot (elements of T): two buffers of the four
