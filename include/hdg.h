@@ -221,11 +221,11 @@ hdg_status hdg_solve_adjoint(hdg_ctx* ctx, int nrhs, const double* h_lambda, con
 hdg_status hdg_set_x1_segment(hdg_ctx* ctx, int elements);
 
 /* Tuning (not part of the method): number of element slots per CTA of the
- * operator kernels (each slot is n^2 threads); 0 restores the automatic
- * choice.  Speed only.  Errors: INVALID_ARG (NULL context, negative count,
- * or a count whose CTA would exceed 320 threads); an FP32 apply whose CTA
- * would exceed 256 threads (n <= 16) fails with CUDA (invalid
- * configuration).                                                          */
+ * element-run operator kernels (each slot is n^2 threads); 0 restores the
+ * automatic choice.  Speed only.  Errors: INVALID_ARG (NULL context,
+ * negative count, or a count whose CTA would exceed 320 threads); an FP32
+ * apply whose CTA would exceed 256 threads (n <= 16) fails with CUDA
+ * (invalid configuration).                                                 */
 hdg_status hdg_set_slots_per_cta(hdg_ctx* ctx, int slots);
 
 /* Autotuner (not part of the method): times the operator kernel of `prec`
@@ -244,6 +244,16 @@ hdg_status hdg_autotune(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_prec
  * 2 always computed in the kernel (FP32 only; FP64 always uses the table).
  * Results agree to FP32 rounding.  Errors: INVALID_ARG.                    */
 hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
+
+/* Tuning (not part of the method): work split of the FP32 operator kernel.
+ * 0 automatic (element runs), 1 element runs (one thread per x1-line, runs
+ * of elements per CTA slot; slots and run length from hdg_set_slots_per_cta
+ * and hdg_set_x1_segment), 2 x2-planes (one thread per x2-plane of an
+ * element, n threads per element, elements_per_cta elements per CTA, 0 =
+ * automatic).  Same arithmetic per point; results agree to FP32 rounding.
+ * Errors: INVALID_ARG (NULL context, variant outside 0..2, or a plane CTA
+ * above 128 threads).                                                      */
+hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant, int elements_per_cta);
 
 /* Measurement support (not part of the method).  Kernel classes:
  *   0 condensed operator, FP32 arithmetic   1 condensed operator, FP64

@@ -17,7 +17,7 @@ BASIS = {"nodal": 0, "transformed": 1}
 EXPORTED = ["hdg_setup", "hdg_destroy", "hdg_trace_size", "hdg_volume_size", "hdg_boundary_size",
             "hdg_get_nodes", "hdg_apply", "hdg_apply_static", "hdg_solve", "hdg_solve_adjoint", "hdg_last_error",
             "hdg_status_string", "hdg_profile", "hdg_profile_read", "hdg_set_x1_segment", "hdg_set_dz_mode",
-            "hdg_set_slots_per_cta", "hdg_autotune"]
+            "hdg_set_slots_per_cta", "hdg_autotune", "hdg_set_operator_variant"]
 
 
 class HdgMesh(ctypes.Structure):
@@ -87,6 +87,8 @@ def lib():
     L.hdg_autotune.restype = ci
     L.hdg_set_dz_mode.argtypes = [vp, ci]
     L.hdg_set_dz_mode.restype = ci
+    L.hdg_set_operator_variant.argtypes = [vp, ci, ci]
+    L.hdg_set_operator_variant.restype = ci
     L.hdg_set_x1_segment.argtypes = [vp, ci]
     L.hdg_set_x1_segment.restype = ci
     L.hdg_profile.argtypes = [vp, ci]

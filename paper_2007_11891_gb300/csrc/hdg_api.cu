@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/hdg.h"
@@ -104,6 +105,8 @@ struct hdg_ctx {
   DevBuf loopctl;   // device loop-trip counter of the CG loop graph
   int seg_override = 0;   // x1 segment length; 0 = automatic
   int ppb_override = 0;   // slots per CTA; 0 = automatic
+  int op_variant = 0;     // FP32 apply kernel: 0 automatic, 1 element runs, 2 x2-planes
+  int plane_epc = 0;      // x2-plane kernel: elements per CTA; 0 = automatic
   int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
 };
 
@@ -246,6 +249,13 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mod
     a.nseg = (c->mesh.ne[0] + a.seg - 1) / a.seg;
   }
   a.max_grid = ctas;
+  // FP32 apply kernel variant: element runs unless x2-planes are asked for
+  // (the planes measured slower on the 16^3, p = 8 workload)
+  if (std::is_same<ST, float>::value && mode == hdg::TPT_APPLY) {
+    const int want = c->op_variant != 0 ? c->op_variant : 1;
+    a.variant = want == 2 ? 1 : 0;
+    if (a.variant == 1) a.ppb = c->plane_epc > 0 ? c->plane_epc : std::max(1, 64 / c->n);
+  }
   // FP32 apply: equal contiguous runs, one per slot of a resident wave (per
   // right-hand side: the wave is shared by the batch)
   const long long nelem = (long long)c->nelem * std::max(nrhs, 1);
@@ -898,6 +908,14 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
   if (h_best_segment) *h_best_segment = best_seg;
   if (h_best_slots) *h_best_slots = best_ppb;
   if (h_best_us) *h_best_us = best;
+  return HDG_OK;
+}
+
+hdg_status hdg_set_operator_variant(hdg_ctx* c, int variant, int elements_per_cta) {
+  if (!c || variant < 0 || variant > 2 || elements_per_cta < 0 || elements_per_cta * c->n > 128)
+    return fail(HDG_ERR_INVALID_ARG, "NULL context, variant outside 0..2 or x2-plane CTA above 128 threads");
+  c->op_variant = variant;
+  c->plane_epc = elements_per_cta;
   return HDG_OK;
 }
 

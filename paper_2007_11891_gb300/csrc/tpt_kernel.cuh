@@ -182,6 +182,7 @@ struct TptArgs {
   const int* skip;              // per rhs: nonzero -> do nothing (converged), or null
   CgHook hook;                  // partials == null: no dot
   int pdl;                      // host: launch with programmatic stream serialization
+  int variant;                  // FP32 apply: 0 element runs (tpt_fast.cuh), 1 x2-planes (tpt_plane.cuh)
 };
 
 // Shared memory per pencil slot (elements of T): two buffers of the four

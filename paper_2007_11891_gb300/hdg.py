@@ -110,6 +110,13 @@ class HDG:
         code = {"auto": 0, "table": 1, "kernel": 2}[mode]
         _capi.check(_capi.lib().hdg_set_dz_mode(self._h, code), "hdg_set_dz_mode")
 
+    def set_operator_variant(self, variant, elements_per_cta=0):
+        """FP32 operator tuning: 'auto', 'runs' (one thread per x1-line) or
+        'planes' (one thread per x2-plane; elements_per_cta, 0 = automatic)."""
+        code = {"auto": 0, "runs": 1, "planes": 2}[variant]
+        _capi.check(_capi.lib().hdg_set_operator_variant(self._h, code, int(elements_per_cta)),
+                    "hdg_set_operator_variant")
+
     # -- measurement -------------------------------------------------------------
     KERNEL_CLASSES = {"op_fp32": 0, "op_fp64": 1, "face": 2, "volume": 3, "rhs_recover": 4, "vector": 5}
 

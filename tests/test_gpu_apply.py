@@ -208,3 +208,38 @@ def test_apply_bf16_storage(ne, bc, p, stretched):
     assert torch.equal(h.apply(x, 1.5, basis="transformed"), y)   # independent of the runs
     with pytest.raises(Exception):
         h.apply(x, 1.5, basis="nodal")
+
+
+@pytest.mark.parametrize("variant", ["runs", "planes"])
+@pytest.mark.parametrize("name,ne,bc,p,stretched,lam,tau", CASES[1:7], ids=[c[0] for c in CASES[1:7]])
+def test_apply_fp32_variants_match_oracle(variant, name, ne, bc, p, stretched, lam, tau):
+    # both FP32 work splits (one thread per x1-line in element runs, one
+    # thread per x2-plane) against the oracle, and bitwise repeatable
+    h, pr = _pair(ne, bc, p, stretched, lam, tau)
+    h.set_operator_variant(variant)
+    x = hdg_inputs.uniform_pm1(h.trace_size, 5)
+    xt = torch.tensor(x, device="cuda", dtype=torch.float32)
+    y = h.apply(xt, lam)
+    ref = pr.apply(x)
+    assert np.abs(y.double().cpu().numpy() - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert torch.equal(h.apply(xt, lam), y)
+    for dz in ("table", "kernel"):
+        h.set_dz_mode(dz)
+        yt = h.apply(xt, lam, basis="transformed")
+        assert torch.equal(h.apply(xt, lam, basis="transformed"), yt)
+
+
+def test_planes_solve_matches_runs_solve():
+    from paper_2007_11891_gb300 import HDG
+    ne, p, lam = (6, 5, 4), 6, 2.0
+    grid = _grid(ne, True, 31)
+    f = torch.tensor(hdg_inputs.gaussian(6 * 5 * 4 * 7 ** 3, 31), device="cuda")
+    out = {}
+    for variant in ("runs", "planes"):
+        h = HDG(ne, grid, (0,) * 6, p, 25.0)
+        h.set_operator_variant(variant)
+        tr, u, info = h.solve(f, lam, tol=1e-11, inner="fp32")
+        assert info[0]["status"] == "OK"
+        out[variant] = u
+    ref = out["runs"].abs().max().item()
+    assert (out["planes"] - out["runs"]).abs().max().item() <= 1e-8 * ref
