@@ -122,33 +122,45 @@ __device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, double 
   __syncthreads();
   if (last) {
     __threadfence();
-    const volatile double* pp = hook.partials + (long long)rhs * gridDim.x;
-    double s = 0.0;
-    for (unsigned int b = tid; b < gridDim.x; b += blockDim.x) s += pp[b];
-    s = warp_sum(s);
-    __syncthreads();
-    if ((tid & 31) == 0) wsum[tid >> 5] = s;
-    __syncthreads();
-    double t = 0.0;
-    if (tid == 0)
-      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += wsum[w];
-    if (hook.cg) {
-      // gamma from the previous update step's partials (fixed order)
-      double g = 0.0;
-      if (hook.cg[rhs].ops > 0) {
-        const double* gp = hook.step_partials + (long long)rhs * hook.step_blocks;
-        for (int b = tid; b < hook.step_blocks; b += blockDim.x) g += gp[b];
-        g = warp_sum(g);
-        __syncthreads();
-        if ((tid & 31) == 0) wsum[tid >> 5] = g;
-        __syncthreads();
-        g = 0.0;
-        if (tid == 0)
-          for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) g += wsum[w];
+    // both sets of partials (this launch's x^T K x and, inside the CG loop,
+    // the previous update's gamma) are loaded in one batch, bypassing L1
+    // (__ldcg), and reduced together in a fixed order
+    const double* pp = hook.partials + (long long)rhs * gridDim.x;
+    const bool want_g = hook.cg != nullptr && hook.cg[rhs].ops > 0;
+    const double* gp = want_g ? hook.step_partials + (long long)rhs * hook.step_blocks : nullptr;
+    const int ng = want_g ? hook.step_blocks : 0;
+    constexpr int K = 8;   // partials per thread per batch
+    double s = 0.0, g = 0.0;
+    for (int b0 = 0; b0 < (int)gridDim.x || b0 < ng; b0 += K * blockDim.x) {
+      double sv[K], gv[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const int b = b0 + q * blockDim.x + tid;
+        sv[q] = b < (int)gridDim.x ? __ldcg(pp + b) : 0.0;
+        gv[q] = b < ng ? __ldcg(gp + b) : 0.0;
       }
-      if (tid == 0) cg_scalars(hook.cg + rhs, hook.flags + rhs, t, g);
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        s += sv[q];
+        g += gv[q];
+      }
     }
+    __shared__ double gsum[16];
+    s = warp_sum(s);
+    g = warp_sum(g);
+    __syncthreads();
+    if ((tid & 31) == 0) {
+      wsum[tid >> 5] = s;
+      gsum[tid >> 5] = g;
+    }
+    __syncthreads();
     if (tid == 0) {
+      double t = 0.0, gt = 0.0;
+      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
+        t += wsum[w];
+        gt += gsum[w];
+      }
+      if (hook.cg) cg_scalars(hook.cg + rhs, hook.flags + rhs, t, gt);
       hook.pq[rhs] = t;
       hook.counter[rhs] = 0u;
     }
