@@ -52,6 +52,8 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   // everything below reads what the previous kernel in the stream wrote
   grid_dep_wait();
   if (a.skip && a.skip[rhs]) return;   // uniform per block
+  __shared__ CgScalars s_cg;
+  const HookPre hpre = hook_prefetch(a.hook, rhs, &s_cg);
 
   const int tid = threadIdx.x;
   const int slot = tid / N2;
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   }
 
   grid_dep_launch();   // the next kernel's blocks may take this block's place
-  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot);
+  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot, hpre, &s_cg);
 }
 
 }  // namespace hdg

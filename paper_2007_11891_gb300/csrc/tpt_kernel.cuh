@@ -63,8 +63,9 @@ struct CgHook {
 // here.  Then alpha_i = gamma_i / (delta_i - beta_i gamma_i / alpha_{i-1})
 // (delta_0 alone for i = 0).  A non-positive or non-finite denominator is a
 // breakdown (status 6).  flags[r] mirrors done.
-__device__ __forceinline__ void cg_scalars(CgScalars* cgp, int* flag, double delta, double gamma_new) {
-  CgScalars c = *cgp;
+__device__ __forceinline__ void cg_scalars(CgScalars* cgp, const CgScalars& c0, int* flag, double delta,
+                                           double gamma_new) {
+  CgScalars c = c0;
   if (c.done) return;
   if (c.ops > 0) {
     c.it = c.ops;
@@ -104,7 +105,25 @@ __device__ __forceinline__ T warp_sum(T v) {
 // of (S sum + D dif) from every thread's `dot`; the last block to finish sums
 // the per-block partials in a fixed order (deterministic) and stores the
 // result (and the CG step scalars when hook.cg is set).
-__device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, double dot) {
+// Start of an operator launch inside the CG loop: what the last block will
+// need from before this launch (the scalar state, and this thread's share of
+// the previous update's gamma partials, which are complete by now) is loaded
+// while the block still has its elements to compute, so that the reduction
+// at the end has one dependent global round trip instead of three.
+struct HookPre {
+  double g;   // this thread's share of the gamma partials
+};
+__device__ __forceinline__ HookPre hook_prefetch(const CgHook& hook, int rhs, CgScalars* s_cg) {
+  HookPre pre{0.0};
+  if (hook.partials == nullptr || hook.cg == nullptr) return pre;
+  if (threadIdx.x == 0) *s_cg = hook.cg[rhs];
+  const double* gp = hook.step_partials + (long long)rhs * hook.step_blocks;
+  for (int b = threadIdx.x; b < hook.step_blocks; b += blockDim.x) pre.g += __ldcg(gp + b);
+  return pre;
+}
+
+__device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, double dot, const HookPre& pre,
+                                            const CgScalars* s_cg) {
   __shared__ double wsum[16];
   __shared__ bool last;
   const int tid = threadIdx.x;
@@ -118,32 +137,29 @@ __device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, double 
     __threadfence();
     const unsigned int done = atomicAdd(hook.counter + rhs, 1u);
     last = (done == gridDim.x - 1);
+    // acquire side of the arrival, in the one thread that observed it (the
+    // other threads of the block have outstanding reductions of their own to
+    // the output, which a fence of theirs would wait for); the block's reads
+    // below go to L2 (__ldcg) after the barrier
+    if (last) __threadfence();
   }
   __syncthreads();
   if (last) {
-    __threadfence();
-    // both sets of partials (this launch's x^T K x and, inside the CG loop,
-    // the previous update's gamma) are loaded in one batch, bypassing L1
-    // (__ldcg), and reduced together in a fixed order
+    // this launch's partials in one batch, bypassing L1 (__ldcg); gamma's
+    // were summed per thread at the start of the launch (hook_prefetch)
     const double* pp = hook.partials + (long long)rhs * gridDim.x;
-    const bool want_g = hook.cg != nullptr && hook.cg[rhs].ops > 0;
-    const double* gp = want_g ? hook.step_partials + (long long)rhs * hook.step_blocks : nullptr;
-    const int ng = want_g ? hook.step_blocks : 0;
     constexpr int K = 8;   // partials per thread per batch
-    double s = 0.0, g = 0.0;
-    for (int b0 = 0; b0 < (int)gridDim.x || b0 < ng; b0 += K * blockDim.x) {
-      double sv[K], gv[K];
+    double s = 0.0;
+    double g = pre.g;
+    for (int b0 = 0; b0 < (int)gridDim.x; b0 += K * blockDim.x) {
+      double sv[K];
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         const int b = b0 + q * blockDim.x + tid;
         sv[q] = b < (int)gridDim.x ? __ldcg(pp + b) : 0.0;
-        gv[q] = b < ng ? __ldcg(gp + b) : 0.0;
       }
 #pragma unroll
-      for (int q = 0; q < K; ++q) {
-        s += sv[q];
-        g += gv[q];
-      }
+      for (int q = 0; q < K; ++q) s += sv[q];
     }
     __shared__ double gsum[16];
     s = warp_sum(s);
@@ -160,7 +176,7 @@ __device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, double 
         t += wsum[w];
         gt += gsum[w];
       }
-      if (hook.cg) cg_scalars(hook.cg + rhs, hook.flags + rhs, t, gt);
+      if (hook.cg) cg_scalars(hook.cg + rhs, *s_cg, hook.flags + rhs, t, gt);
       hook.pq[rhs] = t;
       hook.counter[rhs] = 0u;
     }
@@ -229,6 +245,8 @@ __global__ void __launch_bounds__(320, sizeof(T) == 4 ? 3 : 2) tpt_kernel(const 
 
   const int rhs = blockIdx.y;
   if (a.skip && a.skip[rhs]) return;   // uniform per block: no barrier is skipped partially
+  __shared__ CgScalars s_cg;
+  const HookPre hpre = (MODE == TPT_APPLY) ? hook_prefetch(a.hook, rhs, &s_cg) : HookPre{0.0};
 
   const int tid = threadIdx.x;
   const int slot = tid / N2;
@@ -437,7 +455,7 @@ __global__ void __launch_bounds__(320, sizeof(T) == 4 ? 3 : 2) tpt_kernel(const 
   __syncthreads();   // the next group restages the face buffers
   }  // slot groups
 
-  if (MODE == TPT_APPLY && a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot);
+  if (MODE == TPT_APPLY && a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot, hpre, &s_cg);
 }
 
 }  // namespace hdg

@@ -47,6 +47,8 @@ __global__ void __launch_bounds__(128, 3) tpt_plane_kernel(const TptArgs<float, 
   const int rhs = blockIdx.y;
   grid_dep_wait();   // everything below reads what the previous kernel wrote
   if (a.skip && a.skip[rhs]) return;
+  __shared__ CgScalars s_cg;
+  const HookPre hpre = hook_prefetch(a.hook, rhs, &s_cg);
 
   const int tid = threadIdx.x;
   const int slot = tid / N;
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(128, 3) tpt_plane_kernel(const TptArgs<float, 
   }
 
   grid_dep_launch();
-  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot);
+  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot, hpre, &s_cg);
 }
 
 }  // namespace hdg
