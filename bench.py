@@ -333,7 +333,8 @@ def run_sweep(args):
     {2, 4, 8, 12, 16}, FP64 and FP32, transformed basis, L2 flushed per
     launch) against its roofline, the paper's manufactured solver test
     (8^3 on (0, 2 pi)^3, lambda = 0, p = 2..16: iterations, error, time per
-    unknown), and the 64-rhs batched solve (24^3, p = 7, lambda from
+    unknown), the BF16-stored apply (32^3, p = 8), the adjoint solve (32^3,
+    p = 6), and the 64-rhs batched solve (24^3, p = 7, lambda from
     {0.1, 1, 100}) mixed vs FP64."""
     import torch
     from paper_2007_11891_gb300 import HDG
@@ -407,6 +408,42 @@ def run_sweep(args):
                               "ns_per_unknown_iteration": ms * 1e6 / T / max(info[0]["iterations"], 1)}),
                   flush=True)
         h.close()
+    # BF16-stored operator (transformed basis), 32^3, p = 8: FP32 arithmetic, half the bytes
+    cfg = hdg_inputs.WORKLOADS["uniform32"]
+    ne = cfg["ne"]
+    h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, 8, hdg_inputs.TAU_HAT)
+    xb = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device=dev).to(torch.bfloat16)
+    yb = torch.empty_like(xb)
+    h.apply(xb, cfg["lam"], basis="transformed", out=yb)
+    ms = per_launch_ms(lambda: h.apply(xb, cfg["lam"], basis="transformed", out=yb), 10)
+    ach = 2.0 * h.trace_size * 2 / (ms * 1e-3) / 1e9
+    print(json.dumps({"sweep": "operator", "workload": "uniform32", "p": 8, "precision": "bf16-stored",
+                      "trace_dofs": h.trace_size, "us_per_apply": ms * 1e3,
+                      "gdofs": h.trace_size / (ms * 1e-3) / 1e9,
+                      "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                   "frac": ach / pk["hbm_gbs"], "peak_source": "of " + src}}), flush=True)
+    h.close()
+    del xb, yb
+    # adjoint (32^3, p = 6, lambda = 5): forward solve, L = ||u - u_t||^2, adjoint solve
+    cfg = hdg_inputs.WORKLOADS["adjoint32_p6"]
+    ne, p = cfg["ne"], cfg["p"]
+    h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, p, hdg_inputs.TAU_HAT)
+    f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11897), device=dev)
+    ut = torch.tensor(hdg_inputs.smooth_target(h.volume_coords(), hdg_inputs.smooth_target_coeffs()), device=dev)
+    for inner in ("fp32", "fp64"):
+        fwd = lambda: h.solve(f, cfg["lam"], tol=1e-10, inner=inner)
+        _, u, info_f = fwd()
+        ms_f = per_launch_ms(fwd, 2)
+        gu = 2.0 * (u - ut)
+        adj = lambda: h.solve_adjoint(u, gu, cfg["lam"], tol=1e-10, inner=inner)
+        _, gl, info_a = adj()
+        ms_a = per_launch_ms(adj, 2)
+        print(json.dumps({"sweep": "adjoint", "workload": "adjoint32_p6", "inner": inner, "trace_dofs": h.trace_size,
+                          "forward_ms": ms_f, "adjoint_ms": ms_a, "forward_iterations": info_f[0]["iterations"],
+                          "adjoint_iterations": info_a[0]["iterations"],
+                          "loss": float(((u - ut) ** 2).sum()), "dL_dlambda": float(gl[0]),
+                          "status": [info_f[0]["status"], info_a[0]["status"]]}), flush=True)
+    h.close()
     # batched solve
     cfg = hdg_inputs.WORKLOADS["batched24_p7"]
     ne, p, nrhs = cfg["ne"], cfg["p"], cfg["nrhs"]
