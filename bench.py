@@ -36,6 +36,11 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 # counts and maximum clock); measured 1.19 TFLOP/s at 1987 MHz with an FMA loop
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
+# capture summarised in profiles/tpt_fast_kernel_fp32_cg_loop_stretched16_p8.md
+# (cold caches; the D_Z^-1 table of the stretched grid is most of the excess
+# over the 2 T x 4 B algorithmic bytes)
+TRAFFIC_BYTES = {"op_fp32": 22.76e6}
 
 
 def peaks():
@@ -263,8 +268,9 @@ def run_ours(args, rank, world, local_rank):
         if kind == "op_fp32":
             byts = 2.0 * T * 4
             ach = byts / avg_s / 1e9
-            return {"kernel": "tpt_kernel<float> (operator, FP32)", "bound": "hbm", "achieved": ach,
-                    "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None,
+            return {"kernel": "tpt_fast_kernel<float> (operator, FP32)", "bound": "hbm", "achieved": ach,
+                    "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                    "traffic": TRAFFIC_BYTES["op_fp32"],
                     "peak_source": "of " + src, "avg_launch_us": avg_s * 1e6,
                     "algorithmic_bytes_per_launch": byts}
         if kind == "op_fp64":
