@@ -45,44 +45,6 @@ __device__ __forceinline__ void st4<double>(double* p, const double v[4]) {
   reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
 }
 
-// ---- face transforms: y_f = scale (W (x) W) x_f (Sec. 4.2 basis change) ------
-template <typename TI, typename TO, int N>
-__global__ void face_transform_kernel(const TI* __restrict__ x, TO* __restrict__ y, long long nfaces,
-                                      long long sx, long long sy, const Mat1D<TO> W, TO scale,
-                                      int accumulate, int fpb) {
-  constexpr int N2 = N * N;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TO* sm = reinterpret_cast<TO*>(smem_raw);
-  const int slot = threadIdx.x / N2;
-  const int q = threadIdx.x - slot * N2;
-  const long long face = (long long)blockIdx.x * fpb + slot;
-  const bool act = slot < fpb && face < nfaces;
-  const int r = blockIdx.y;
-  TO* X = sm + (act ? slot : 0) * 2 * N2;
-  TO* Tm = X + N2;
-  const int a1 = q % N, a2 = q / N;
-  if (act) X[q] = load_as<TI, TO>(x + r * sx + face * N2 + q);
-  __syncthreads();
-  if (act) {
-    // T[c2][a1] = sum_c1 W[a1][c1] X[c2][c1]   (q = a1 + N c2)
-    TO t = TO(0);
-#pragma unroll
-    for (int c1 = 0; c1 < N; ++c1) t = fma(W.a[a1 * N + c1], X[a2 * N + c1], t);
-    Tm[q] = t;
-  }
-  __syncthreads();
-  if (act) {
-    // Y[a2][a1] = sum_c2 W[a2][c2] T[c2][a1]
-    TO v = TO(0);
-#pragma unroll
-    for (int c2 = 0; c2 < N; ++c2) v = fma(W.a[a2 * N + c2], Tm[c2 * N + a1], v);
-    v *= scale;
-    TO* dst = y + r * sy + face * N2 + q;
-    if (accumulate) v += *dst;
-    *dst = v;
-  }
-}
-
 // ---- volume transforms: y_e = s_e (A (x) A (x) A) x_e -------------------------
 // One 1D line transform out[a] = sum_i A[a][i] in[i] of n values.
 // PAR = 0: dense, n^2 multiply-adds.  The basis-change matrices inherit the
@@ -94,11 +56,11 @@ __global__ void face_transform_kernel(const TI* __restrict__ x, TO* __restrict__
 //   out[i] = E_i + O_i and out[n-1-i] = E_i - O_i with the even- and
 //   odd-mode partial sums E_i, O_i.
 // Either parity form takes about n^2 / 2 multiply-adds.
-template <int N, int PAR>
-__device__ __forceinline__ void line_transform(const Mat1D<double>& A, const double (&in)[N], double (&out)[N]) {
+template <int N, int PAR, typename T>
+__device__ __forceinline__ void line_transform(const Mat1D<T>& A, const T (&in)[N], T (&out)[N]) {
   constexpr int NE = (N + 1) / 2, H = N / 2;
   if constexpr (PAR == 1) {
-    double sp[NE], dm[H > 0 ? H : 1];
+    T sp[NE], dm[H > 0 ? H : 1];
 #pragma unroll
     for (int i = 0; i < H; ++i) {
       sp[i] = in[i] + in[N - 1 - i];
@@ -107,7 +69,7 @@ __device__ __forceinline__ void line_transform(const Mat1D<double>& A, const dou
     if constexpr (N % 2 == 1) sp[H] = in[H];
 #pragma unroll
     for (int a = 0; a < N; ++a) {
-      double v = 0.0;
+      T v = T(0);
       if (a < NE) {
 #pragma unroll
         for (int i = 0; i < NE; ++i) v = fma(A.a[a * N + i], sp[i], v);
@@ -120,7 +82,7 @@ __device__ __forceinline__ void line_transform(const Mat1D<double>& A, const dou
   } else if constexpr (PAR == 2) {
 #pragma unroll
     for (int i = 0; i < NE; ++i) {
-      double ev = 0.0, od = 0.0;
+      T ev = T(0), od = T(0);
 #pragma unroll
       for (int m = 0; m < NE; ++m) ev = fma(A.a[i * N + m], in[m], ev);
 #pragma unroll
@@ -131,10 +93,53 @@ __device__ __forceinline__ void line_transform(const Mat1D<double>& A, const dou
   } else {
 #pragma unroll
     for (int a = 0; a < N; ++a) {
-      double v = 0.0;
+      T v = T(0);
 #pragma unroll
       for (int i = 0; i < N; ++i) v = fma(A.a[a * N + i], in[i], v);
       out[a] = v;
+    }
+  }
+}
+
+// ---- face transforms (Sec. 4.2 basis change), one thread per face row:
+//      y_f = scale (W (x) W) x_f ------------------------------------------------
+// Thread l of a face first transforms row l (T[l][.] = W x[l][.]), then,
+// after a barrier, column l (y[.][l] = scale W T[.][l]); both with the
+// line transform above, so the matrix entries are compile-time operands and
+// mirror-symmetric matrices take the parity-split form.
+template <typename TI, typename TO, int N, int PAR>
+__global__ void face_rows_kernel(const TI* __restrict__ x, TO* __restrict__ y, long long nfaces, long long sx,
+                                 long long sy, const Mat1D<TO> W, TO scale, int accumulate, int fpb) {
+  constexpr int N2 = N * N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TO* sm = reinterpret_cast<TO*>(smem_raw);
+  const int slot = threadIdx.x / N;
+  const int l = threadIdx.x - slot * N;
+  const long long face = (long long)blockIdx.x * fpb + slot;
+  const bool act = slot < fpb && face < nfaces;
+  const int r = blockIdx.y;
+  TO* Tm = sm + (act ? slot : 0) * N2;   // T[row][a1]
+  if (act) {
+    const TI* xf = x + r * sx + face * N2 + N * l;
+    TO in[N], out[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) in[c] = load_as<TI, TO>(xf + c);
+    line_transform<N, PAR>(W, in, out);
+#pragma unroll
+    for (int a = 0; a < N; ++a) Tm[N * l + a] = out[a];
+  }
+  __syncthreads();
+  if (act) {
+    TO in[N], out[N];
+#pragma unroll
+    for (int c = 0; c < N; ++c) in[c] = Tm[N * c + l];
+    line_transform<N, PAR>(W, in, out);
+    TO* yf = y + r * sy + face * N2 + l;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+      TO v = scale * out[a];
+      if (accumulate) v += yf[N * a];
+      yf[N * a] = v;
     }
   }
 }
@@ -547,21 +552,6 @@ __global__ void cg_pupdate_kernel(const CgScalars* cg, T* __restrict__ p, const 
   }
 }
 
-template <typename TI, typename TO, int N>
-cudaError_t ft_one(const TI* x, TO* y, long long nfaces, int nrhs, long long sx, long long sy,
-                   const Mat1D<double>& Wd, double scale, int accumulate, cudaStream_t s) {
-  Mat1D<TO> W;
-  for (int i = 0; i < N * N; ++i) W.a[i] = static_cast<TO>(Wd.a[i]);
-  const int fpb = (256 / (N * N)) > 0 ? 256 / (N * N) : 1;
-  const int threads = (fpb * N * N + 31) / 32 * 32;
-  const size_t smem = (size_t)fpb * 2 * N * N * sizeof(TO);
-  dim3 grid((unsigned)((nfaces + fpb - 1) / fpb), nrhs);
-  if (nfaces <= 0) return cudaSuccess;
-  face_transform_kernel<TI, TO, N><<<grid, threads, smem, s>>>(x, y, nfaces, sx, sy, W,
-                                                               static_cast<TO>(scale), accumulate, fpb);
-  return cudaGetLastError();
-}
-
 // Mirror-symmetry form of A (see line_transform): 1 rows, 2 columns, 0 none.
 // Checked to a relative 1e-13 of the largest entry; the parity kernels then
 // use only the first half of each row or column.
@@ -578,6 +568,33 @@ int matrix_parity(int n, const Mat1D<double>& A) {
       col = col && fabs(A.a[(n - 1 - a) * n + i] - si * A.a[a * n + i]) <= tol;
     }
   return row ? 1 : (col ? 2 : 0);
+}
+
+template <typename TI, typename TO, int N, int PAR>
+cudaError_t ft_launch(const TI* x, TO* y, long long nfaces, int nrhs, long long sx, long long sy,
+                      const Mat1D<TO>& W, TO scale, int accumulate, cudaStream_t s) {
+  const int fpb = std::max(1, 256 / N);
+  const int threads = (fpb * N + 31) / 32 * 32;
+  const size_t smem = (size_t)fpb * N * N * sizeof(TO);
+  if (smem > kSmemOptIn)
+    cudaFuncSetAttribute(face_rows_kernel<TI, TO, N, PAR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)((nfaces + fpb - 1) / fpb), nrhs);
+  if (nfaces <= 0) return cudaSuccess;
+  face_rows_kernel<TI, TO, N, PAR><<<grid, threads, smem, s>>>(x, y, nfaces, sx, sy, W, scale, accumulate, fpb);
+  return cudaGetLastError();
+}
+
+template <typename TI, typename TO, int N>
+cudaError_t ft_one(const TI* x, TO* y, long long nfaces, int nrhs, long long sx, long long sy,
+                   const Mat1D<double>& Wd, double scale, int accumulate, cudaStream_t s) {
+  Mat1D<TO> W;
+  for (int i = 0; i < N * N; ++i) W.a[i] = static_cast<TO>(Wd.a[i]);
+  const TO sc = static_cast<TO>(scale);
+  switch (matrix_parity(N, Wd)) {
+    case 1: return ft_launch<TI, TO, N, 1>(x, y, nfaces, nrhs, sx, sy, W, sc, accumulate, s);
+    case 2: return ft_launch<TI, TO, N, 2>(x, y, nfaces, nrhs, sx, sy, W, sc, accumulate, s);
+    default: return ft_launch<TI, TO, N, 0>(x, y, nfaces, nrhs, sx, sy, W, sc, accumulate, s);
+  }
 }
 
 template <int N, int PAR>
