@@ -106,7 +106,7 @@ typedef struct {
   double inner_tol;        /* floor of the relative residual reduction asked of one
                               inner solve; each inner solve targets
                               max(floor, tol ||F|| / (2 ||r||)) for the current
-                              outer residual r; <= 0 picks 1e-6 (FP32) or 0 (FP64) */
+                              outer residual r; <= 0 picks 3e-4 (FP32) or 0 (FP64) */
   int precond;             /* 0: plain CG; 1: face-block Jacobi preconditioner of
                               Sec. 5.1 (Alg. hdg_pc_block), diagonal in the
                               transformed basis (the paper's HDG-trans solver)     */

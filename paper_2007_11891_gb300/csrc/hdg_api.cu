@@ -651,9 +651,12 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
   if (!(o.tol > 0.0) || o.max_iter < 1 || o.max_outer < 1) return fail(HDG_ERR_INVALID_ARG, "bad solve options");
   if (o.inner == HDG_BF16) return fail(HDG_ERR_UNSUPPORTED, "BF16 inner solve is not available");
   // each inner solve targets max(floor, tol ||F|| / (2 ||r||)) per rhs: just
-  // enough for the refinement to meet the tolerance, but not below what the
-  // inner precision resolves
-  const double tol_floor = o.inner_tol > 0.0 ? o.inner_tol : (o.inner == HDG_FP64 ? 0.0 : 1e-6);
+  // enough for the refinement to meet the tolerance.  FP32 floor 3e-4: three
+  // refinement steps of about 3.5 decades each stay clear of the region
+  // where FP32 CG slows down near its accuracy limit (measured: 309 inner
+  // iterations at 3e-4 against 346 at 1e-6 on a 16^3 p = 8 stretched mesh,
+  // 606 against 701 on 32^3 p = 6; looser floors add refinement steps)
+  const double tol_floor = o.inner_tol > 0.0 ? o.inner_tol : (o.inner == HDG_FP64 ? 0.0 : 3e-4);
   for (int r = 0; r < nrhs; ++r)
     if (lam[r] == 0.0 && !c->has_dirichlet)
       return fail(HDG_ERR_SINGULAR, "lambda = 0 without a Dirichlet side: the condensed operator is singular");

@@ -517,8 +517,17 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
       acc = fma(un, rn, acc);
     }
   }
-  const double sblk = block_sum(static_cast<double>(acc));
-  if (threadIdx.x == 0) partials[(long long)r * gridDim.x + blockIdx.x] = sblk;
+  // warp sums in T (FP64 arithmetic is slow on this part), then FP64 across warps
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, m);
+  __shared__ double wsum[8];
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = static_cast<double>(acc);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sblk = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) sblk += wsum[w];
+    partials[(long long)r * gridDim.x + blockIdx.x] = sblk;
+  }
 }
 
 template <typename T>

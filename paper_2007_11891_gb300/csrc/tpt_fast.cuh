@@ -253,7 +253,7 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   }
 
   grid_dep_launch();   // the next kernel's blocks may take this block's place
-  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot, hpre, &s_cg);
+  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, dot, hpre, &s_cg);
 }
 
 }  // namespace hdg

@@ -101,10 +101,6 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// End of an operator launch with a hook: x^T y = 1/2 sum over element faces
-// of (S sum + D dif) from every thread's `dot`; the last block to finish sums
-// the per-block partials in a fixed order (deterministic) and stores the
-// result (and the CG step scalars when hook.cg is set).
 // Start of an operator launch inside the CG loop: what the last block will
 // need from before this launch (the scalar state, and this thread's share of
 // the previous update's gamma partials, which are complete by now) is loaded
@@ -117,18 +113,29 @@ __device__ __forceinline__ HookPre hook_prefetch(const CgHook& hook, int rhs, Cg
   HookPre pre{0.0};
   if (hook.partials == nullptr || hook.cg == nullptr) return pre;
   if (threadIdx.x == 0) *s_cg = hook.cg[rhs];
-  const double* gp = hook.step_partials + (long long)rhs * hook.step_blocks;
-  for (int b = threadIdx.x; b < hook.step_blocks; b += blockDim.x) pre.g += __ldcg(gp + b);
+  if (threadIdx.x < 32) {   // the warp that would finish the reduction
+    const double* gp = hook.step_partials + (long long)rhs * hook.step_blocks;
+    for (int b = threadIdx.x; b < hook.step_blocks; b += 32) pre.g += __ldcg(gp + b);
+  }
   return pre;
 }
 
-__device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, double dot, const HookPre& pre,
+// End of an operator launch with a hook.  The per-thread x^T y contributions
+// (1/2 sum over element faces of (S sum + D dif)) are summed per warp in the
+// kernel's own precision T, per block and across blocks in FP64, all in a
+// fixed order.  FP64 arithmetic runs at a small fraction of the FP32 rate on
+// this part, so the cross-block reduction in the last block is done by one
+// warp (about 15 partials per lane) rather than by the whole block.  The last
+// block to arrive stores the result (and the CG step scalars when hook.cg is
+// set); the summation order is fixed, so the result is deterministic.
+template <typename T>
+__device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, T dot, const HookPre& pre,
                                             const CgScalars* s_cg) {
-  __shared__ double wsum[16];
+  __shared__ double wsum[32];
   __shared__ bool last;
   const int tid = threadIdx.x;
-  const double v = warp_sum(dot);
-  if ((tid & 31) == 0) wsum[tid >> 5] = v;
+  const T v = warp_sum(dot);
+  if ((tid & 31) == 0) wsum[tid >> 5] = static_cast<double>(v);
   __syncthreads();
   if (tid == 0) {
     double s = 0.0;
@@ -139,45 +146,30 @@ __device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, double 
     last = (done == gridDim.x - 1);
     // acquire side of the arrival, in the one thread that observed it (the
     // other threads of the block have outstanding reductions of their own to
-    // the output, which a fence of theirs would wait for); the block's reads
-    // below go to L2 (__ldcg) after the barrier
+    // the output, which a fence of theirs would wait for); the reads below
+    // go to L2 (__ldcg) after the barrier
     if (last) __threadfence();
   }
   __syncthreads();
-  if (last) {
-    // this launch's partials in one batch, bypassing L1 (__ldcg); gamma's
-    // were summed per thread at the start of the launch (hook_prefetch)
+  if (last && tid < 32) {
     const double* pp = hook.partials + (long long)rhs * gridDim.x;
-    constexpr int K = 8;   // partials per thread per batch
+    constexpr int K = 16;   // partials per lane per batch
     double s = 0.0;
-    double g = pre.g;
-    for (int b0 = 0; b0 < (int)gridDim.x; b0 += K * blockDim.x) {
+    for (int b0 = 0; b0 < (int)gridDim.x; b0 += K * 32) {
       double sv[K];
 #pragma unroll
       for (int q = 0; q < K; ++q) {
-        const int b = b0 + q * blockDim.x + tid;
+        const int b = b0 + q * 32 + tid;
         sv[q] = b < (int)gridDim.x ? __ldcg(pp + b) : 0.0;
       }
 #pragma unroll
       for (int q = 0; q < K; ++q) s += sv[q];
     }
-    __shared__ double gsum[16];
     s = warp_sum(s);
-    g = warp_sum(g);
-    __syncthreads();
-    if ((tid & 31) == 0) {
-      wsum[tid >> 5] = s;
-      gsum[tid >> 5] = g;
-    }
-    __syncthreads();
+    const double g = warp_sum(pre.g);
     if (tid == 0) {
-      double t = 0.0, gt = 0.0;
-      for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
-        t += wsum[w];
-        gt += gsum[w];
-      }
-      if (hook.cg) cg_scalars(hook.cg + rhs, *s_cg, hook.flags + rhs, t, gt);
-      hook.pq[rhs] = t;
+      if (hook.cg) cg_scalars(hook.cg + rhs, *s_cg, hook.flags + rhs, s, g);
+      hook.pq[rhs] = s;
       hook.counter[rhs] = 0u;
     }
   }
@@ -455,7 +447,7 @@ __global__ void __launch_bounds__(320, sizeof(T) == 4 ? 3 : 2) tpt_kernel(const 
   __syncthreads();   // the next group restages the face buffers
   }  // slot groups
 
-  if (MODE == TPT_APPLY && a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot, hpre, &s_cg);
+  if (MODE == TPT_APPLY && a.hook.partials != nullptr) hook_finish(a.hook, rhs, dot, hpre, &s_cg);
 }
 
 }  // namespace hdg

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(128, 3) tpt_plane_kernel(const TptArgs<float, 
   }
 
   grid_dep_launch();
-  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, (double)dot, hpre, &s_cg);
+  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, dot, hpre, &s_cg);
 }
 
 }  // namespace hdg
