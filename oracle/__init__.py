@@ -23,10 +23,15 @@ linearly scaling operator", arXiv:2007.11891):
 * ``solver``    -- the global apply sum_e Q_e^T K_e Q_e, the right-hand side
                    and recovery of Alg. (hdg_cg) (signs from block
                    elimination), plain CG, and the discrete adjoint.
+* ``lowdim``    -- the same construction in one and two directions: the 1D
+                   system of Eq. (ldg_element_operator) and its Schur
+                   complement Eq. (hdg_operator_oned), the 2D system from the
+                   blocks of Tab. (hdg_matrices_threed) with one direction
+                   fewer, global apply and a direct solve.
 
 It shares no code with the CUDA path: no eigen-decomposition, no
 sum factorisation, no fast diagonalisation.  Every pin it is checked against
 lives in ``tests/test_oracle_*.py``.
 """
 
-from . import basis1d, element3d, mesh, solver  # noqa: F401
+from . import basis1d, element3d, lowdim, mesh, solver  # noqa: F401
