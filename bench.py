@@ -341,7 +341,10 @@ def run_sweep(args):
     (8^3 on (0, 2 pi)^3, lambda = 0, p = 2..16: iterations, error, time per
     unknown), the BF16-stored apply (32^3, p = 8), the adjoint solve (32^3,
     p = 6), and the 64-rhs batched solve (24^3, p = 7, lambda from
-    {0.1, 1, 100}) mixed vs FP64."""
+    {0.1, 1, 100}) mixed vs FP64; also the nodal-basis FP64 apply at 32^3
+    (face-wise transforms against one kernel per apply) and the 1D/2D
+    operators.  ``--parts``
+    selects sections."""
     import torch
     from paper_2007_11891_gb300 import HDG
     dev = torch.device("cuda", 0)
@@ -362,109 +365,165 @@ def run_sweep(args):
             tot += e0.elapsed_time(e1)
         return tot / reps
 
-    cfg = hdg_inputs.WORKLOADS["uniform32"]
-    ne = cfg["ne"]
-    grid = hdg_inputs.grid_lines(ne)
-    for p in (2, 4, 8, 12, 16):
-        h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
-        T = h.trace_size
-        n = p + 1
-        x64 = torch.tensor(hdg_inputs.uniform_pm1(T, 11893), device=dev)
-        for prec, x in (("fp64", x64), ("fp32", x64.float())):
-            y = torch.empty_like(x)
-            h.apply(x, cfg["lam"], basis="transformed", out=y)
-            ms = per_launch_ms(lambda: h.apply(x, cfg["lam"], basis="transformed", out=y), 10)
-            line = {"sweep": "operator", "workload": "uniform32", "p": p, "precision": prec,
-                    "trace_dofs": T, "us_per_apply": ms * 1e3, "gdofs": T / (ms * 1e-3) / 1e9}
-            if prec == "fp32":
-                ach = 2.0 * T * 4 / (ms * 1e-3) / 1e9
-                line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                                    "frac": ach / pk["hbm_gbs"], "peak_source": "of " + src}
-            else:
-                flops = (12.0 * n ** 3 + 24.0 * n ** 2) * ne[0] * ne[1] * ne[2]
-                ach = flops / (ms * 1e-3) / 1e12
-                line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                    "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "derived FP64 pipe"}
-            print(json.dumps(line), flush=True)
-        h.close()
-        del x64
-    # the paper's solver test (Sec. 5.3): 8^3 elements on (0, 2 pi)^3, lambda = 0,
-    # inhomogeneous Dirichlet data from u_ex (k = 5), residual reduced by 1e-10
-    cfg = hdg_inputs.WORKLOADS["paper_case"]
-    ne = cfg["ne"]
-    grid = hdg_inputs.grid_lines(ne, length=cfg["length"])
-    for p in range(2, 17):
-        h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
-        X = h.volume_coords()
-        f = torch.tensor(hdg_inputs.paper_case_load(X, cfg["lam"]), device=dev)
-        bd = torch.tensor(hdg_inputs.paper_case_u(h.boundary_coords()[0]), device=dev)
-        uex = hdg_inputs.paper_case_u(X)
-        for inner in ("fp32", "fp64"):
-            run = lambda: h.solve(f, cfg["lam"], bdry=bd, tol=1e-10, inner=inner)
-            run()
-            ms = per_launch_ms(run, 3)
-            _, u, info = run()
+    parts = set(args.parts.split(","))
+    if "operator" in parts:
+        cfg = hdg_inputs.WORKLOADS["uniform32"]
+        ne = cfg["ne"]
+        grid = hdg_inputs.grid_lines(ne)
+        for p in (2, 4, 8, 12, 16):
+            h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
             T = h.trace_size
-            print(json.dumps({"sweep": "paper_case", "workload": "paper_case", "p": p, "inner": inner,
-                              "trace_dofs": T, "ms": ms, "iterations": info[0]["iterations"],
-                              "outer": info[0]["outer"], "rel_residual": info[0]["rel_residual"],
-                              "status": info[0]["status"],
-                              "max_error": float(np.abs(u.cpu().numpy() - uex).max()),
-                              "ns_per_unknown": ms * 1e6 / T,
-                              "ns_per_unknown_iteration": ms * 1e6 / T / max(info[0]["iterations"], 1)}),
-                  flush=True)
+            n = p + 1
+            x64 = torch.tensor(hdg_inputs.uniform_pm1(T, 11893), device=dev)
+            for prec, x in (("fp64", x64), ("fp32", x64.float())):
+                y = torch.empty_like(x)
+                h.apply(x, cfg["lam"], basis="transformed", out=y)
+                ms = per_launch_ms(lambda: h.apply(x, cfg["lam"], basis="transformed", out=y), 10)
+                line = {"sweep": "operator", "workload": "uniform32", "p": p, "precision": prec,
+                        "trace_dofs": T, "us_per_apply": ms * 1e3, "gdofs": T / (ms * 1e-3) / 1e9}
+                if prec == "fp32":
+                    ach = 2.0 * T * 4 / (ms * 1e-3) / 1e9
+                    line["roofline"] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                        "frac": ach / pk["hbm_gbs"], "peak_source": "of " + src}
+                else:
+                    flops = (12.0 * n ** 3 + 24.0 * n ** 2) * ne[0] * ne[1] * ne[2]
+                    ach = flops / (ms * 1e-3) / 1e12
+                    line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                        "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "derived FP64 pipe"}
+                print(json.dumps(line), flush=True)
+            h.close()
+            del x64
+    if "nodal" in parts:
+        # nodal-basis FP64 apply, 32^3 uniform: face-wise transforms around the
+        # transformed kernel (three launches) against one kernel per apply
+        # (Alg. hdg_op_3d, each element transforms its own faces)
+        cfg = hdg_inputs.WORKLOADS["uniform32"]
+        ne = cfg["ne"]
+        grid = hdg_inputs.grid_lines(ne)
+        for p in (2, 4, 8, 12, 16):
+            h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
+            T = h.trace_size
+            n = p + 1
+            nel = ne[0] * ne[1] * ne[2]
+            x = torch.tensor(hdg_inputs.uniform_pm1(T, 11893), device=dev)
+            y = torch.empty_like(x)
+            for variant, fl in (("facewise", 36.0 * n ** 3 + 24.0 * n ** 2), ("fused", 60.0 * n ** 3 + 24.0 * n ** 2)):
+                h.set_nodal_variant(variant)
+                h.apply(x, cfg["lam"], basis="nodal", out=y)
+                ms = per_launch_ms(lambda: h.apply(x, cfg["lam"], basis="nodal", out=y), 5)
+                ach = fl * nel / (ms * 1e-3) / 1e12
+                print(json.dumps({"sweep": "nodal_apply", "workload": "uniform32", "p": p, "variant": variant,
+                                  "trace_dofs": T, "us_per_apply": ms * 1e3, "gdofs": T / (ms * 1e-3) / 1e9,
+                                  "flops_per_element": fl,
+                                  "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                                               "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                                               "peak_source": "derived FP64 pipe"}}), flush=True)
+            h.close()
+            del x, y
+    if "lowdim" in parts:
+        # 1D (Alg. hdg_op_1d) and 2D operators, FP64, uniform grids, lambda = 1,
+        # Dirichlet sides: 10^6 elements at p = 8 (1D), 512 x 512 at p = 8 (2D)
+        from paper_2007_11891_gb300 import HDGLowDim
+        for ne in ((1000000,), (512, 512)):
+            p = 8
+            grid = [np.linspace(0.0, 1.0, v + 1) for v in ne]
+            h = HDGLowDim(ne, grid, (0,) * (2 * len(ne)), p, hdg_inputs.TAU_HAT)
+            T = h.trace_size
+            nel = int(np.prod(ne))
+            x = torch.tensor(hdg_inputs.uniform_pm1(T, 11893), device=dev)
+            y = torch.empty_like(x)
+            for basis in ("nodal", "transformed") if len(ne) == 2 else ("nodal",):
+                h.apply(x, 1.0, basis=basis, out=y)
+                ms = per_launch_ms(lambda: h.apply(x, 1.0, basis=basis, out=y), 10)
+                byt = 2.0 * T * 8 + 32.0 * nel   # traces in and out, metric factors
+                ach = byt / (ms * 1e-3) / 1e9
+                print(json.dumps({"sweep": "lowdim_apply", "dim": len(ne), "ne": list(ne), "p": p, "basis": basis,
+                                  "trace_dofs": T, "us_per_apply": ms * 1e3, "gdofs": T / (ms * 1e-3) / 1e9,
+                                  "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                               "frac": ach / pk["hbm_gbs"], "peak_source": "of " + src}}), flush=True)
+            h.close()
+            del x, y
+    if "paper" in parts:
+        # the paper's solver test (Sec. 5.3): 8^3 elements on (0, 2 pi)^3, lambda = 0,
+        # inhomogeneous Dirichlet data from u_ex (k = 5), residual reduced by 1e-10
+        cfg = hdg_inputs.WORKLOADS["paper_case"]
+        ne = cfg["ne"]
+        grid = hdg_inputs.grid_lines(ne, length=cfg["length"])
+        for p in range(2, 17):
+            h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
+            X = h.volume_coords()
+            f = torch.tensor(hdg_inputs.paper_case_load(X, cfg["lam"]), device=dev)
+            bd = torch.tensor(hdg_inputs.paper_case_u(h.boundary_coords()[0]), device=dev)
+            uex = hdg_inputs.paper_case_u(X)
+            for inner in ("fp32", "fp64"):
+                run = lambda: h.solve(f, cfg["lam"], bdry=bd, tol=1e-10, inner=inner)
+                run()
+                ms = per_launch_ms(run, 3)
+                _, u, info = run()
+                T = h.trace_size
+                print(json.dumps({"sweep": "paper_case", "workload": "paper_case", "p": p, "inner": inner,
+                                  "trace_dofs": T, "ms": ms, "iterations": info[0]["iterations"],
+                                  "outer": info[0]["outer"], "rel_residual": info[0]["rel_residual"],
+                                  "status": info[0]["status"],
+                                  "max_error": float(np.abs(u.cpu().numpy() - uex).max()),
+                                  "ns_per_unknown": ms * 1e6 / T,
+                                  "ns_per_unknown_iteration": ms * 1e6 / T / max(info[0]["iterations"], 1)}),
+                      flush=True)
+            h.close()
+    if "bf16" in parts:
+        # BF16-stored operator (transformed basis), 32^3, p = 8: FP32 arithmetic, half the bytes
+        cfg = hdg_inputs.WORKLOADS["uniform32"]
+        ne = cfg["ne"]
+        h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, 8, hdg_inputs.TAU_HAT)
+        xb = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device=dev).to(torch.bfloat16)
+        yb = torch.empty_like(xb)
+        h.apply(xb, cfg["lam"], basis="transformed", out=yb)
+        ms = per_launch_ms(lambda: h.apply(xb, cfg["lam"], basis="transformed", out=yb), 10)
+        ach = 2.0 * h.trace_size * 2 / (ms * 1e-3) / 1e9
+        print(json.dumps({"sweep": "operator", "workload": "uniform32", "p": 8, "precision": "bf16-stored",
+                          "trace_dofs": h.trace_size, "us_per_apply": ms * 1e3,
+                          "gdofs": h.trace_size / (ms * 1e-3) / 1e9,
+                          "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                       "frac": ach / pk["hbm_gbs"], "peak_source": "of " + src}}), flush=True)
         h.close()
-    # BF16-stored operator (transformed basis), 32^3, p = 8: FP32 arithmetic, half the bytes
-    cfg = hdg_inputs.WORKLOADS["uniform32"]
-    ne = cfg["ne"]
-    h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, 8, hdg_inputs.TAU_HAT)
-    xb = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device=dev).to(torch.bfloat16)
-    yb = torch.empty_like(xb)
-    h.apply(xb, cfg["lam"], basis="transformed", out=yb)
-    ms = per_launch_ms(lambda: h.apply(xb, cfg["lam"], basis="transformed", out=yb), 10)
-    ach = 2.0 * h.trace_size * 2 / (ms * 1e-3) / 1e9
-    print(json.dumps({"sweep": "operator", "workload": "uniform32", "p": 8, "precision": "bf16-stored",
-                      "trace_dofs": h.trace_size, "us_per_apply": ms * 1e3,
-                      "gdofs": h.trace_size / (ms * 1e-3) / 1e9,
-                      "roofline": {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                                   "frac": ach / pk["hbm_gbs"], "peak_source": "of " + src}}), flush=True)
-    h.close()
-    del xb, yb
-    # adjoint (32^3, p = 6, lambda = 5): forward solve, L = ||u - u_t||^2, adjoint solve
-    cfg = hdg_inputs.WORKLOADS["adjoint32_p6"]
-    ne, p = cfg["ne"], cfg["p"]
-    h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, p, hdg_inputs.TAU_HAT)
-    f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11897), device=dev)
-    ut = torch.tensor(hdg_inputs.smooth_target(h.volume_coords(), hdg_inputs.smooth_target_coeffs()), device=dev)
-    for inner in ("fp32", "fp64"):
-        fwd = lambda: h.solve(f, cfg["lam"], tol=1e-10, inner=inner)
-        _, u, info_f = fwd()
-        ms_f = per_launch_ms(fwd, 2)
-        gu = 2.0 * (u - ut)
-        adj = lambda: h.solve_adjoint(u, gu, cfg["lam"], tol=1e-10, inner=inner)
-        _, gl, info_a = adj()
-        ms_a = per_launch_ms(adj, 2)
-        print(json.dumps({"sweep": "adjoint", "workload": "adjoint32_p6", "inner": inner, "trace_dofs": h.trace_size,
-                          "forward_ms": ms_f, "adjoint_ms": ms_a, "forward_iterations": info_f[0]["iterations"],
-                          "adjoint_iterations": info_a[0]["iterations"],
-                          "loss": float(((u - ut) ** 2).sum()), "dL_dlambda": float(gl[0]),
-                          "status": [info_f[0]["status"], info_a[0]["status"]]}), flush=True)
-    h.close()
-    # batched solve
-    cfg = hdg_inputs.WORKLOADS["batched24_p7"]
-    ne, p, nrhs = cfg["ne"], cfg["p"], cfg["nrhs"]
-    h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, p, hdg_inputs.TAU_HAT)
-    lams = hdg_inputs.batch_lambdas(nrhs)
-    F = torch.tensor(np.stack([hdg_inputs.gaussian(h.volume_size, 11894 + r) for r in range(nrhs)]), device=dev)
-    for inner in ("fp32", "fp64"):
-        h.solve(F, lams, tol=1e-10, inner=inner)
-        ms = per_launch_ms(lambda: h.solve(F, lams, tol=1e-10, inner=inner), 2)
-        _, _, info = h.solve(F, lams, tol=1e-10, inner=inner)
-        print(json.dumps({"sweep": "batched_solve", "workload": "batched24_p7", "nrhs": nrhs, "inner": inner,
-                          "ms": ms, "trace_dofs_per_rhs": h.trace_size,
-                          "max_iterations": max(i["iterations"] for i in info),
-                          "max_rel_residual": max(i["rel_residual"] for i in info),
-                          "all_ok": all(i["status"] == "OK" for i in info)}), flush=True)
+        del xb, yb
+    if "adjoint" in parts:
+        # adjoint (32^3, p = 6, lambda = 5): forward solve, L = ||u - u_t||^2, adjoint solve
+        cfg = hdg_inputs.WORKLOADS["adjoint32_p6"]
+        ne, p = cfg["ne"], cfg["p"]
+        h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, p, hdg_inputs.TAU_HAT)
+        f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11897), device=dev)
+        ut = torch.tensor(hdg_inputs.smooth_target(h.volume_coords(), hdg_inputs.smooth_target_coeffs()), device=dev)
+        for inner in ("fp32", "fp64"):
+            fwd = lambda: h.solve(f, cfg["lam"], tol=1e-10, inner=inner)
+            _, u, info_f = fwd()
+            ms_f = per_launch_ms(fwd, 2)
+            gu = 2.0 * (u - ut)
+            adj = lambda: h.solve_adjoint(u, gu, cfg["lam"], tol=1e-10, inner=inner)
+            _, gl, info_a = adj()
+            ms_a = per_launch_ms(adj, 2)
+            print(json.dumps({"sweep": "adjoint", "workload": "adjoint32_p6", "inner": inner, "trace_dofs": h.trace_size,
+                              "forward_ms": ms_f, "adjoint_ms": ms_a, "forward_iterations": info_f[0]["iterations"],
+                              "adjoint_iterations": info_a[0]["iterations"],
+                              "loss": float(((u - ut) ** 2).sum()), "dL_dlambda": float(gl[0]),
+                              "status": [info_f[0]["status"], info_a[0]["status"]]}), flush=True)
+        h.close()
+    if "batched" in parts:
+        # batched solve
+        cfg = hdg_inputs.WORKLOADS["batched24_p7"]
+        ne, p, nrhs = cfg["ne"], cfg["p"], cfg["nrhs"]
+        h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, p, hdg_inputs.TAU_HAT)
+        lams = hdg_inputs.batch_lambdas(nrhs)
+        F = torch.tensor(np.stack([hdg_inputs.gaussian(h.volume_size, 11894 + r) for r in range(nrhs)]), device=dev)
+        for inner in ("fp32", "fp64"):
+            h.solve(F, lams, tol=1e-10, inner=inner)
+            ms = per_launch_ms(lambda: h.solve(F, lams, tol=1e-10, inner=inner), 2)
+            _, _, info = h.solve(F, lams, tol=1e-10, inner=inner)
+            print(json.dumps({"sweep": "batched_solve", "workload": "batched24_p7", "nrhs": nrhs, "inner": inner,
+                              "ms": ms, "trace_dofs_per_rhs": h.trace_size,
+                              "max_iterations": max(i["iterations"] for i in info),
+                              "max_rel_residual": max(i["rel_residual"] for i in info),
+                              "all_ok": all(i["status"] == "OK" for i in info)}), flush=True)
 
 
 def run_probe(args):
@@ -504,6 +563,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sweep", action="store_true", help="extra measurements instead of the bench line")
+    ap.add_argument("--parts", default="operator,nodal,lowdim,paper,bf16,adjoint,batched",
+                    help="sweep sections to run (comma-separated)")
     ap.add_argument("--probe", choices=["solve", "apply32", "apply64"], help="untimed workload for ncu")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(hdg_inputs.WORKLOADS))
     ap.add_argument("--eager", action="store_true",

@@ -255,6 +255,20 @@ hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
  * above 128 threads).                                                      */
 hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant, int elements_per_cta);
 
+/* Which kernel applies K in the nodal basis (hdg_apply with HDG_FP64 and
+ * HDG_BASIS_NODAL):
+ *   0 (default) face-wise: every unknown face is transformed to the face
+ *     eigenbasis once (S^T M (x) S^T M), the transformed operator of
+ *     Alg. (hdg_op_3d_transformed) runs, and every face is transformed back
+ *     (M S (x) M S): three launches, 49 n^3 flops per element, two trace-
+ *     sized temporaries;
+ *   1 one kernel per apply, Alg. (hdg_op_3d) (the paper's HDG-TP, Sec. 4.2):
+ *     each element transforms its own six faces in and out, 73 n^3 flops
+ *     per element (Tab. operator_variants), no temporaries.
+ * Both give K x to FP64 rounding.  Other precisions and bases ignore it.
+ * Errors: INVALID_ARG (NULL context, variant outside 0..1).               */
+hdg_status hdg_set_nodal_variant(hdg_ctx* ctx, int variant);
+
 /* Measurement support (not part of the method).  Kernel classes:
  *   0 condensed operator, FP32 arithmetic   1 condensed operator, FP64
  *   2 face transforms                       3 volume transforms
@@ -272,6 +286,51 @@ hdg_status hdg_profile_read(hdg_ctx* ctx, int kernel_class, double* total_ms, lo
 /* Message of the last failed call on this host thread ("" if none).      */
 const char* hdg_last_error(void);
 const char* hdg_status_string(hdg_status s);
+
+/* ---- One- and two-dimensional meshes ---------------------------------------
+ * The condensed operator K of Eq. (hdg_system) for lambda u - u'' = f on an
+ * interval split into ne[0] elements (dim = 1, Alg. (hdg_op_1d), Sec. 2.2),
+ * and for lambda u - laplace u = f on a rectangle of ne[0] x ne[1]
+ * rectangular elements (dim = 2: Alg. (hdg_op_3d) / (hdg_op_3d_transformed)
+ * with one direction fewer).  Same 1D tables, penalty tau = 2 tau_hat / h
+ * and mass options as the three-dimensional context; apply only.
+ *
+ * Trace layout (device, double): faces normal to direction d lie on grid
+ * planes 0..ne[d]; a plane is an unknown unless it is a boundary plane of a
+ * Dirichlet side.  Block d (d = 0, then 1) holds the unknown planes in
+ * order; in 2D each plane holds ne[1-d] faces (one per element along the
+ * other axis, in order) of n = p + 1 GLL nodes along that axis; in 1D each
+ * plane is one value.  hdg_lowdim_trace_size() values per right-hand side.
+ */
+typedef struct hdg_lowdim hdg_lowdim;
+
+typedef struct {
+  int dim;                 /* 1 or 2                                             */
+  int ne[2];               /* elements per direction, >= 1 (ne[1] unused if dim = 1) */
+  const double* h_grid[2]; /* host; ne[d] + 1 strictly increasing coordinates    */
+  int bc[4];               /* sides x1-, x1+, x2-, x2+ (the last two unused if
+                              dim = 1): 0 Dirichlet, 1 Neumann                   */
+} hdg_lowdim_mesh;
+
+/* Build a 1D/2D context (opts may be NULL: tau_hat 25, exact mass).  Errors:
+ * INVALID_ARG (NULL pointers, dim outside 1..2, empty direction, grid not
+ * increasing, bc not 0/1), UNSUPPORTED (p outside 1..16, not sm_103, trace
+ * above 2^31 - 1), CUDA, OOM.  *out owns device memory until
+ * hdg_lowdim_destroy.                                                      */
+hdg_status hdg_lowdim_setup(const hdg_lowdim_mesh* mesh, int p, const hdg_options* opts, hdg_lowdim** out);
+size_t hdg_lowdim_trace_size(const hdg_lowdim* ctx);
+
+/* y_r = K(lambda_r) x_r, r < nrhs, FP64, on `stream` (asynchronous; the
+ * lambdas are copied before return).  d_x, d_y: device, nrhs blocks of
+ * hdg_lowdim_trace_size() values, caller-owned, not overlapping; d_y is
+ * overwritten.  basis: HDG_BASIS_NODAL (GLL nodal values on the faces) or
+ * HDG_BASIS_TRANSFORMED (face eigenbasis S^-1 x per edge in 2D); in 1D the
+ * faces are single points and both give the same K.  Errors: INVALID_ARG
+ * (NULL pointers, nrhs outside 1..65535, lambda < 0 or not finite, bad
+ * basis), CUDA.                                                            */
+hdg_status hdg_lowdim_apply(hdg_lowdim* ctx, int nrhs, const double* h_lambda, hdg_basis basis, const double* d_x,
+                            double* d_y, void* stream);
+void hdg_lowdim_destroy(hdg_lowdim* ctx);
 
 #ifdef __cplusplus
 }

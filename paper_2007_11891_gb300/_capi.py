@@ -17,7 +17,14 @@ BASIS = {"nodal": 0, "transformed": 1}
 EXPORTED = ["hdg_setup", "hdg_destroy", "hdg_trace_size", "hdg_volume_size", "hdg_boundary_size",
             "hdg_get_nodes", "hdg_apply", "hdg_apply_static", "hdg_solve", "hdg_solve_adjoint", "hdg_last_error",
             "hdg_status_string", "hdg_profile", "hdg_profile_read", "hdg_set_x1_segment", "hdg_set_dz_mode",
-            "hdg_set_slots_per_cta", "hdg_autotune", "hdg_set_operator_variant"]
+            "hdg_set_slots_per_cta", "hdg_autotune", "hdg_set_operator_variant",
+            "hdg_set_nodal_variant", "hdg_lowdim_setup", "hdg_lowdim_trace_size", "hdg_lowdim_apply",
+            "hdg_lowdim_destroy"]
+
+
+class HdgLowDimMesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("ne", ctypes.c_int * 2), ("h_grid", ctypes.POINTER(ctypes.c_double) * 2),
+                ("bc", ctypes.c_int * 4)]
 
 
 class HdgMesh(ctypes.Structure):
@@ -89,6 +96,17 @@ def lib():
     L.hdg_set_dz_mode.restype = ci
     L.hdg_set_operator_variant.argtypes = [vp, ci, ci]
     L.hdg_set_operator_variant.restype = ci
+    L.hdg_set_nodal_variant.argtypes = [vp, ci]
+    L.hdg_set_nodal_variant.restype = ci
+    L.hdg_lowdim_setup.argtypes = [ctypes.POINTER(HdgLowDimMesh), ci, ctypes.POINTER(HdgOptions),
+                                   ctypes.POINTER(vp)]
+    L.hdg_lowdim_setup.restype = ci
+    L.hdg_lowdim_trace_size.argtypes = [vp]
+    L.hdg_lowdim_trace_size.restype = ctypes.c_size_t
+    L.hdg_lowdim_apply.argtypes = [vp, ci, ctypes.POINTER(ctypes.c_double), ci, vp, vp, vp]
+    L.hdg_lowdim_apply.restype = ci
+    L.hdg_lowdim_destroy.argtypes = [vp]
+    L.hdg_lowdim_destroy.restype = None
     L.hdg_set_x1_segment.argtypes = [vp, ci]
     L.hdg_set_x1_segment.restype = ci
     L.hdg_profile.argtypes = [vp, ci]

@@ -106,6 +106,7 @@ struct hdg_ctx {
   int seg_override = 0;   // x1 segment length; 0 = automatic
   int ppb_override = 0;   // slots per CTA; 0 = automatic
   int op_variant = 0;     // FP32 apply kernel: 0 automatic, 1 element runs, 2 x2-planes
+  int nodal_variant = 0;  // FP64 nodal apply: 0 face-wise transforms + transformed kernel, 1 one kernel (HDG-TP)
   int plane_epc = 0;      // x2-plane kernel: elements per CTA; 0 = automatic
   int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
 };
@@ -295,6 +296,30 @@ hdg_status tpt_apply(hdg_ctx* c, int nrhs, const T* dinv, const ST* x, ST* y, cu
                                   ", n=" + std::to_string(c->n) + ", slots=" + std::to_string(a.ppb) +
                                   ", seg=" + std::to_string(a.seg) + "x" + std::to_string(a.nseg) +
                                   ", run=" + std::to_string(a.chunk) + ", grid cap=" + std::to_string(a.max_grid) +
+                                  ", nrhs=" + std::to_string(nrhs) + "): " + cudaGetErrorString(e));
+  return HDG_OK;
+}
+
+// Nodal-basis FP64 apply in one kernel (Alg. hdg_op_3d): no workspace; the
+// output is zeroed and receives the element contributions by atomic adds
+hdg_status nodal_apply(hdg_ctx* c, int nrhs, const double* dinv, const double* x, double* y, cudaStream_t s) {
+  hdg::NodalArgs a{};
+  a.mesh = c->mesh;
+  a.tab = tables<double>(c);
+  a.StM = c->StM;
+  a.MS = c->MS;
+  a.metric = metric_ptr<double>(c);
+  a.dinv = dinv;
+  a.dinv_rhs_stride = nclass(c) * dz_table<double>(c);
+  a.lam = static_cast<const double*>(lam_buf<double>(c).p);
+  a.x = x;
+  a.y = y;
+  a.trace_stride = c->ntrace;
+  HDG_CUDA(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)c->ntrace * nrhs, s));
+  Timed t(c, K_OP64, s);
+  const cudaError_t e = hdg::launch_tp_nodal(c->n, a, nrhs, s);
+  if (e != cudaSuccess)
+    return fail(HDG_ERR_CUDA, std::string("nodal operator launch (n=") + std::to_string(c->n) +
                                   ", nrhs=" + std::to_string(nrhs) + "): " + cudaGetErrorString(e));
   return HDG_OK;
 }
@@ -820,6 +845,21 @@ bool ctx_view(const hdg_ctx* c, CtxView* v) {
 void set_last_error(const char* msg) { g_last_error = msg; }
 }  // namespace hdg
 
+// 1D / 2D context (hdg_lowdim_*): mesh bookkeeping, 1D tables, metric
+struct hdg_lowdim {
+  int dim = 1, p = 1, n = 2;
+  int ne[2] = {1, 1};
+  int bc[4] = {0, 0, 0, 0};
+  int lo[2] = {0, 0}, hi[2] = {-1, -1};
+  long long blk[2] = {0, 0};
+  long long ntrace = 0;
+  hdg::Setup1D s1;
+  hdg::Tables<double> tab{};
+  hdg::Mat1D<double> StM{}, MS{};
+  double* d_metric = nullptr;
+  DevBuf lam;
+};
+
 extern "C" {
 
 const char* hdg_last_error(void) { return g_last_error.c_str(); }
@@ -919,6 +959,12 @@ hdg_status hdg_set_operator_variant(hdg_ctx* c, int variant, int elements_per_ct
     return fail(HDG_ERR_INVALID_ARG, "NULL context, variant outside 0..2 or x2-plane CTA above 128 threads");
   c->op_variant = variant;
   c->plane_epc = elements_per_cta;
+  return HDG_OK;
+}
+
+hdg_status hdg_set_nodal_variant(hdg_ctx* c, int variant) {
+  if (!c || variant < 0 || variant > 1) return fail(HDG_ERR_INVALID_ARG, "NULL context or nodal variant outside 0..1");
+  c->nodal_variant = variant;
   return HDG_OK;
 }
 
@@ -1149,6 +1195,7 @@ hdg_status hdg_apply(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precision
     HDG_TRY(ensure_dinv<double>(c, nrhs, h_lambda, s, &dinv));
     if (basis == HDG_BASIS_TRANSFORMED)
       return tpt_apply<double, double>(c, nrhs, dinv, static_cast<const double*>(d_x), static_cast<double*>(d_y), s);
+    if (c->nodal_variant == 1) return nodal_apply(c, nrhs, dinv, static_cast<const double*>(d_x), static_cast<double*>(d_y), s);
     HDG_TRY(ensure(c->ws[W_XHAT], sizeof(double) * tot));
     HDG_TRY(ensure(c->ws[W_YHAT], sizeof(double) * tot));
     double* xh = wsp<double>(c, W_XHAT);
@@ -1222,6 +1269,131 @@ hdg_status hdg_solve_adjoint(hdg_ctx* c, int nrhs, const double* h_lambda, const
   HDG_CUDA(cudaGetLastError());
   HDG_CUDA(cudaStreamSynchronize(s));
   return HDG_OK;
+}
+
+hdg_status hdg_lowdim_setup(const hdg_lowdim_mesh* mesh, int p, const hdg_options* opts, hdg_lowdim** out) {
+  begin_call();
+  if (!mesh || !out) return fail(HDG_ERR_INVALID_ARG, "mesh and out must not be NULL");
+  *out = nullptr;
+  if (mesh->dim != 1 && mesh->dim != 2) return fail(HDG_ERR_INVALID_ARG, "dim must be 1 or 2");
+  if (p < 1 || p > 16) return fail(HDG_ERR_UNSUPPORTED, "degree p must be in 1..16");
+  const int dim = mesh->dim;
+  for (int d = 0; d < dim; ++d) {
+    if (mesh->ne[d] < 1 || !mesh->h_grid[d]) return fail(HDG_ERR_INVALID_ARG, "each direction needs >= 1 element and a grid");
+    for (int i = 0; i < mesh->ne[d]; ++i)
+      if (!(mesh->h_grid[d][i + 1] > mesh->h_grid[d][i])) return fail(HDG_ERR_INVALID_ARG, "grid lines must increase");
+  }
+  for (int sd = 0; sd < 2 * dim; ++sd)
+    if (mesh->bc[sd] != 0 && mesh->bc[sd] != 1) return fail(HDG_ERR_INVALID_ARG, "bc must be 0 (Dirichlet) or 1 (Neumann)");
+  int dev = 0;
+  HDG_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp prop;
+  HDG_CUDA(cudaGetDeviceProperties(&prop, dev));
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(HDG_ERR_UNSUPPORTED, "this library is built for sm_103 (GB300) only");
+  hdg_lowdim* c = new hdg_lowdim();
+  c->dim = dim;
+  c->p = p;
+  c->n = p + 1;
+  const char* msg = "";
+  if (hdg::build_setup1d(p, opts ? opts->tau_hat : 25.0, opts ? opts->mass_lumped : 0, &c->s1, &msg) != 0) {
+    delete c;
+    return fail(HDG_ERR_INVALID_ARG, std::string("1D set-up: ") + msg);
+  }
+  const int n = c->n;
+  for (int d = 0; d < dim; ++d) c->ne[d] = mesh->ne[d];
+  for (int sd = 0; sd < 2 * dim; ++sd) c->bc[sd] = mesh->bc[sd];
+  long long faces = 0;
+  for (int d = 0; d < dim; ++d) {
+    c->lo[d] = c->bc[2 * d] == 1 ? 0 : 1;
+    c->hi[d] = c->bc[2 * d + 1] == 1 ? c->ne[d] : c->ne[d] - 1;
+    c->blk[d] = faces;
+    const long long other = dim == 2 ? c->ne[1 - d] : 1;
+    faces += std::max(0, c->hi[d] - c->lo[d] + 1) * other;
+  }
+  c->ntrace = faces * (dim == 2 ? n : 1);
+  const long long nelem = (long long)c->ne[0] * c->ne[1];
+  if (c->ntrace >= (1LL << 31) || nelem >= (1LL << 31)) {
+    delete c;
+    return fail(HDG_ERR_UNSUPPORTED, "trace size above 2^31 - 1");
+  }
+  for (int i = 0; i < n; ++i) {
+    c->tab.c[i] = c->s1.bs[i];
+    c->tab.lam[i] = c->s1.Lambda[i];
+  }
+  c->tab.h0 = c->s1.h0;
+  c->tab.h1 = c->s1.h1;
+  for (int i = 0; i < n * n; ++i) {
+    c->StM.a[i] = c->s1.StM[i];
+    c->MS.a[i] = c->s1.MS[i];
+  }
+  // metric factors (Sec. 2.2 / 3.2 with dim directions): d0 = prod h/2, d_i = d0 (2/h_i)^2
+  std::vector<double> met(4 * (size_t)nelem, 0.0);
+  for (long long e = 0; e < nelem; ++e) {
+    const int e1 = (int)(e % c->ne[0]), e2 = (int)(e / c->ne[0]);
+    const double h1 = mesh->h_grid[0][e1 + 1] - mesh->h_grid[0][e1];
+    const double h2 = dim == 2 ? mesh->h_grid[1][e2 + 1] - mesh->h_grid[1][e2] : 2.0;
+    const double d0 = h1 * h2 / 4.0;
+    met[4 * e] = d0;
+    met[4 * e + 1] = d0 * (2.0 / h1) * (2.0 / h1);
+    met[4 * e + 2] = dim == 2 ? d0 * (2.0 / h2) * (2.0 / h2) : 0.0;
+  }
+  cudaError_t ce = cudaMalloc(&c->d_metric, sizeof(double) * met.size());
+  if (ce == cudaSuccess) ce = cudaMemcpy(c->d_metric, met.data(), sizeof(double) * met.size(), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    cudaFree(c->d_metric);
+    delete c;
+    return fail(ce == cudaErrorMemoryAllocation ? HDG_ERR_OOM : HDG_ERR_CUDA,
+                std::string("metric upload: ") + cudaGetErrorString(ce));
+  }
+  *out = c;
+  return HDG_OK;
+}
+
+size_t hdg_lowdim_trace_size(const hdg_lowdim* c) { return c ? (size_t)c->ntrace : 0; }
+
+hdg_status hdg_lowdim_apply(hdg_lowdim* c, int nrhs, const double* h_lambda, hdg_basis basis, const double* d_x,
+                            double* d_y, void* stream) {
+  begin_call();
+  if (!c || !d_x || !d_y || nrhs < 1) return fail(HDG_ERR_INVALID_ARG, "NULL pointer or nrhs < 1");
+  if (nrhs > 65535) return fail(HDG_ERR_INVALID_ARG, "nrhs above 65535");
+  if (!h_lambda) return fail(HDG_ERR_INVALID_ARG, "lambda pointer is NULL");
+  for (int r = 0; r < nrhs; ++r)
+    if (!(h_lambda[r] >= 0.0) || !std::isfinite(h_lambda[r])) return fail(HDG_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  if (basis != HDG_BASIS_NODAL && basis != HDG_BASIS_TRANSFORMED) return fail(HDG_ERR_INVALID_ARG, "bad basis");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (c->ntrace == 0) return HDG_OK;
+  HDG_TRY(ensure(c->lam, sizeof(double) * nrhs));
+  HDG_CUDA(cudaMemcpyAsync(c->lam.p, h_lambda, sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+  HDG_CUDA(cudaMemsetAsync(d_y, 0, sizeof(double) * (size_t)c->ntrace * nrhs, s));
+  hdg::LowDimArgs a{};
+  a.dim = c->dim;
+  a.n = c->n;
+  for (int d = 0; d < 2; ++d) {
+    a.ne[d] = c->ne[d];
+    a.lo[d] = c->lo[d];
+    a.hi[d] = c->hi[d];
+    a.blk[d] = c->blk[d];
+  }
+  a.tab = c->tab;
+  a.StM = c->StM;
+  a.MS = c->MS;
+  a.metric = c->d_metric;
+  a.lam = static_cast<const double*>(c->lam.p);
+  a.x = d_x;
+  a.y = d_y;
+  a.trace_stride = c->ntrace;
+  a.nodal = basis == HDG_BASIS_NODAL ? 1 : 0;
+  HDG_CUDA(hdg::launch_lowdim(a, nrhs, s));
+  return HDG_OK;
+}
+
+void hdg_lowdim_destroy(hdg_lowdim* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  cudaFree(c->d_metric);
+  if (c->lam.p) cudaFree(c->lam.p);
+  delete c;
 }
 
 }  // extern "C"

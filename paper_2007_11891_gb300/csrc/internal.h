@@ -25,6 +25,43 @@ void tpt_split(int n, const int ne[3], int nrhs, int ctas, int ppb, int* seg, in
 template <typename T, typename ST>
 int tpt_blocks_per_sm(int mode, int n, int ppb);
 
+// ---- tp_nodal.cu: nodal-basis operator in one kernel (Alg. hdg_op_3d) ------
+struct NodalArgs {
+  MeshDev mesh;
+  Tables<double> tab;
+  Mat1D<double> StM;            // S^T M, [mode][node]
+  Mat1D<double> MS;             // M S, [node][mode]
+  const double* metric;         // d0..d3 per element (one set when uniform)
+  const double* dinv;           // D_Z^-1 table [rhs][class][k][j][i] (padded rows), or null
+  long long dinv_rhs_stride;
+  const double* lam;            // per right-hand side lambda (device; when dinv is null)
+  const double* x;              // nodal unknown-face inputs
+  double* y;                    // nodal unknown-face outputs, zeroed by the caller
+  long long trace_stride;
+  int epb;                      // elements per CTA (set by the launcher)
+};
+// y = K x in the nodal basis for nrhs right-hand sides, y zeroed beforehand
+cudaError_t launch_tp_nodal(int n, const NodalArgs& a, int nrhs, cudaStream_t s);
+
+// ---- lowdim.cu: 1D (Alg. hdg_op_1d) and 2D condensed operators ----------------
+struct LowDimArgs {
+  int dim;                      // 1 or 2
+  int n;                        // p + 1
+  int ne[2];                    // elements per direction (ne[1] = 1 when dim = 1)
+  int lo[2], hi[2];             // unknown planes per direction
+  long long blk[2];             // first face id of each direction block
+  Tables<double> tab;
+  Mat1D<double> StM, MS;        // face transforms (2D nodal basis)
+  const double* metric;         // d0, d1, d2, 0 per element
+  const double* lam;            // per right-hand side lambda (device)
+  const double* x;              // unknown-face inputs
+  double* y;                    // unknown-face outputs, zeroed by the caller
+  long long trace_stride;
+  int nodal;                    // 2D: inputs and outputs in the nodal basis
+  int epb;                      // elements per CTA (set by the launcher)
+};
+cudaError_t launch_lowdim(const LowDimArgs& a, int nrhs, cudaStream_t s);
+
 // ---- kernels.cu ---------------------------------------------------------------
 // y_f = scale (W (x) W) x_f for every face f (n x n nodes, lower axis fastest),
 // optionally y_f += ...;  nfaces faces per right-hand side, strides in values.

@@ -117,6 +117,13 @@ class HDG:
         _capi.check(_capi.lib().hdg_set_operator_variant(self._h, code, int(elements_per_cta)),
                     "hdg_set_operator_variant")
 
+    def set_nodal_variant(self, variant):
+        """FP64 nodal-basis apply: 'facewise' (transform every face once around
+        the transformed operator, three launches) or 'fused' (Alg. hdg_op_3d,
+        each element transforms its own faces, one launch, no workspace)."""
+        code = {"facewise": 0, "fused": 1}[variant]
+        _capi.check(_capi.lib().hdg_set_nodal_variant(self._h, code), "hdg_set_nodal_variant")
+
     # -- measurement -------------------------------------------------------------
     KERNEL_CLASSES = {"op_fp32": 0, "op_fp64": 1, "face": 2, "volume": 3, "rhs_recover": 4, "vector": 5}
 
@@ -240,6 +247,60 @@ class HDG:
                                            ctypes.c_void_p(gl.data_ptr()), ctypes.byref(opts), info, _stream())
         _capi.check(st, "hdg_solve_adjoint")
         return gf.reshape(u.shape), gl, [info[i].as_dict() for i in range(nrhs)]
+
+
+class HDGLowDim:
+    """The condensed operator on a 1D or 2D Cartesian mesh (apply only).
+
+    ne: one or two element counts; grid: that many increasing coordinate
+    arrays of length ne[d] + 1; bc: two or four sides (x1-, x1+[, x2-,
+    x2+]), 0 Dirichlet, 1 Neumann; p: degree 1..16.
+    """
+
+    def __init__(self, ne, grid, bc=None, p=4, tau_hat=25.0, mass_lumped=False):
+        L = _capi.lib()
+        torch.cuda.init()
+        self.ne = tuple(int(v) for v in ne)
+        self.dim = len(self.ne)
+        self.p, self.n = int(p), int(p) + 1
+        bc = (0,) * (2 * self.dim) if bc is None else tuple(int(v) for v in bc)
+        self._grid = [(ctypes.c_double * (self.ne[d] + 1))(*[float(v) for v in grid[d]]) for d in range(self.dim)]
+        m = _capi.HdgLowDimMesh()
+        m.dim = self.dim
+        for d in range(self.dim):
+            m.ne[d] = self.ne[d]
+            m.h_grid[d] = ctypes.cast(self._grid[d], ctypes.POINTER(ctypes.c_double))
+        for s_ in range(2 * self.dim):
+            m.bc[s_] = bc[s_]
+        o = _capi.HdgOptions(float(tau_hat), int(bool(mass_lumped)))
+        h = ctypes.c_void_p()
+        _capi.check(L.hdg_lowdim_setup(ctypes.byref(m), self.p, ctypes.byref(o), ctypes.byref(h)),
+                    "hdg_lowdim_setup")
+        self._h = h
+        self.trace_size = int(L.hdg_lowdim_trace_size(h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _capi.lib().hdg_lowdim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def apply(self, x, lam, basis="nodal", out=None):
+        """y = K x (homogeneous Dirichlet data); x: (T,) or (nrhs, T) float64 CUDA tensor."""
+        x2 = x.reshape(-1, self.trace_size)
+        if not x2.is_cuda or not x2.is_contiguous() or x2.dtype != torch.float64:
+            raise ValueError("x must be a contiguous float64 CUDA tensor")
+        y = torch.empty_like(x2) if out is None else out.reshape(-1, self.trace_size)
+        nrhs = x2.shape[0]
+        st = _capi.lib().hdg_lowdim_apply(self._h, nrhs, _lams(lam, nrhs), _capi.BASIS[basis],
+                                          ctypes.c_void_p(x2.data_ptr()), ctypes.c_void_p(y.data_ptr()), _stream())
+        _capi.check(st, "hdg_lowdim_apply")
+        return y.reshape(x.shape)
 
 
 class HDGSolve(torch.autograd.Function):

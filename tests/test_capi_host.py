@@ -65,3 +65,30 @@ def test_setup_argument_errors(L):
     assert L.hdg_last_error()
     L.hdg_destroy(None)   # no-op
     assert L.hdg_trace_size(None) == 0
+
+
+def test_tuning_setters_reject_null_context(L):
+    assert L.hdg_set_nodal_variant(None, 1) == 1
+    assert L.hdg_set_operator_variant(None, 1, 0) == 1
+    assert L.hdg_set_dz_mode(None, 0) == 1
+
+
+def test_lowdim_setup_argument_errors(L):
+    from paper_2007_11891_gb300 import _capi
+    grid = (ctypes.c_double * 3)(0.0, 0.5, 1.0)
+    m = _capi.HdgLowDimMesh()
+    m.dim = 3
+    m.ne[0] = m.ne[1] = 2
+    for d in range(2):
+        m.h_grid[d] = ctypes.cast(grid, ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    o = _capi.HdgOptions(25.0, 0)
+    assert L.hdg_lowdim_setup(ctypes.byref(m), 2, ctypes.byref(o), ctypes.byref(h)) == 1   # dim
+    m.dim = 2
+    assert L.hdg_lowdim_setup(ctypes.byref(m), 17, ctypes.byref(o), ctypes.byref(h)) == 7  # p
+    m.bc[3] = 2
+    assert L.hdg_lowdim_setup(ctypes.byref(m), 2, ctypes.byref(o), ctypes.byref(h)) == 1   # bc
+    assert L.hdg_lowdim_setup(None, 2, ctypes.byref(o), ctypes.byref(h)) == 1
+    assert h.value is None
+    assert L.hdg_lowdim_trace_size(None) == 0
+    L.hdg_lowdim_destroy(None)

@@ -243,3 +243,52 @@ def test_planes_solve_matches_runs_solve():
         out[variant] = u
     ref = out["runs"].abs().max().item()
     assert (out["planes"] - out["runs"]).abs().max().item() <= 1e-8 * ref
+
+
+# ---- nodal basis in one kernel (Alg. hdg_op_3d, HDG-TP) ------------------------
+@pytest.mark.parametrize("name,ne,bc,p,stretched,lam,tau", CASES, ids=[c[0] for c in CASES])
+def test_apply_fused_nodal_matches_oracle(name, ne, bc, p, stretched, lam, tau):
+    h, pr = _pair(ne, bc, p, stretched, lam, tau)
+    h.set_nodal_variant("fused")
+    if h.trace_size == 0:
+        return
+    x = hdg_inputs.uniform_pm1(h.trace_size, 11893)
+    y = h.apply(torch.tensor(x, device="cuda"), lam).cpu().numpy()
+    ref = pr.apply(x)
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_fused_nodal_batched_deterministic_and_facewise_equal():
+    from paper_2007_11891_gb300 import HDG
+    ne, bc, p = (5, 3, 4), (0, 1, 0, 0, 1, 0), 6
+    grid = _grid(ne, True, 12)
+    h = HDG(ne, grid, bc, p, 25.0)
+    lams = [0.1, 1.0, 100.0, 0.0]
+    X = torch.tensor(np.stack([hdg_inputs.uniform_pm1(h.trace_size, 40 + r) for r in range(4)]), device="cuda")
+    h.set_nodal_variant("fused")
+    Y1 = h.apply(X, lams)
+    Y2 = h.apply(X, lams)
+    assert torch.equal(Y1, Y2)   # two additions per face: order independent
+    h.set_nodal_variant("facewise")
+    Y0 = h.apply(X, lams)
+    for r, lam in enumerate(lams):
+        ref = Problem(ne, grid, bc, p, 25.0, lam).apply(X[r].cpu().numpy())
+        scale = np.abs(ref).max()
+        assert np.abs(Y1[r].cpu().numpy() - ref).max() <= 1e-12 * scale
+        assert float((Y1[r] - Y0[r]).abs().max()) <= 1e-12 * scale
+
+
+def test_fused_nodal_full_size_sampled():
+    from paper_2007_11891_gb300 import HDG
+    cfg = hdg_inputs.WORKLOADS["stretched_p8"]
+    ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"]
+    grid = hdg_inputs.grid_lines(ne, cfg["stretched"])
+    h = HDG(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT)
+    h.set_nodal_variant("fused")
+    pr = Problem(ne, grid, (0,) * 6, p, hdg_inputs.TAU_HAT, lam)
+    x = hdg_inputs.uniform_pm1(h.trace_size, 11893)
+    y = h.apply(torch.tensor(x, device="cuda"), lam).cpu().numpy()
+    rng = np.random.default_rng(5)
+    dofs = np.concatenate([rng.choice(h.trace_size, 12, replace=False), [0, h.trace_size - 1]])
+    ref = pr.apply_rows(x, dofs)
+    assert np.abs(y[dofs] - ref).max() <= 1e-12 * np.abs(ref).max()
