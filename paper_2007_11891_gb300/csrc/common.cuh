@@ -124,6 +124,9 @@ __device__ __forceinline__ void store_from<__nv_bfloat16, float>(__nv_bfloat16* 
 // scheduled once every block of this grid has signalled or exited.
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+// Cache hint: bring the line holding *p into L1 (p must be a valid global
+// address); no register is written.
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 // y += v with a single global reduction (L2 atomic).  Exactly two adds reach
 // an interior face value that starts at zero: 0 + a + b == 0 + b + a in IEEE

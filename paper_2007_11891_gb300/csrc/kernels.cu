@@ -465,25 +465,42 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
                    T* __restrict__ u, T* __restrict__ wv, T* __restrict__ p, T* __restrict__ sv,
                    const T* __restrict__ W, long long len, double* partials) {
   const int r = blockIdx.y;
-  grid_dep_wait();     // the operator launch before this one wrote w, the scalars and flags
-  grid_dep_launch();   // the next operator launch may queue its blocks behind this wave
-  if (flags[r]) return;
   const long long o = r * len;
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nvec = (len % 4 == 0) ? len / 4 : 0;
-  const T zero[4] = {T(0), T(0), T(0), T(0)};
-  T acc = T(0);
-  for (long long v = tid; v < nvec; v += stride) {
-    const long long t = o + 4 * v;
-    T uv[4], wq[4], pv[4], sq[4], xv[4], rv[4], mv[4] = {T(1), T(1), T(1), T(1)};
+  // The first group's u, p, s, x, r and W were written by the update launch
+  // before the operator (complete before the operator's blocks passed their
+  // own wait, hence before this launch began), and the operator does not
+  // write them: they are loaded while the operator's last block is still
+  // reducing.  w, the scalars and the flags are the operator's and are read
+  // after the wait; every store comes after it.
+  T uv[4], wq[4], pv[4], sq[4], xv[4], rv[4], mv[4] = {T(1), T(1), T(1), T(1)};
+  if (tid < nvec) {
+    const long long t = o + 4 * tid;
     ld4(u + t, uv);
-    ld4(wv + t, wq);
     ld4(p + t, pv);
     ld4(sv + t, sq);
     ld4(x + t, xv);
     ld4(rvec + t, rv);
     if (W) ld4(W + t, mv);
+  }
+  grid_dep_wait();     // the operator launch before this one wrote w, the scalars and flags
+  grid_dep_launch();   // the next operator launch may queue its blocks behind this wave
+  if (flags[r]) return;
+  const T zero[4] = {T(0), T(0), T(0), T(0)};
+  T acc = T(0);
+  for (long long v = tid; v < nvec; v += stride) {
+    const long long t = o + 4 * v;
+    if (v != tid) {
+      ld4(u + t, uv);
+      ld4(p + t, pv);
+      ld4(sv + t, sq);
+      ld4(x + t, xv);
+      ld4(rvec + t, rv);
+      if (W) ld4(W + t, mv);
+    }
+    ld4(wv + t, wq);
     const T al = static_cast<T>(cg[r].alpha), be = static_cast<T>(cg[r].beta);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {

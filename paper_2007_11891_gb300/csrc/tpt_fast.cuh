@@ -148,6 +148,9 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
       no = offsets(n1, n2, n3);
     }
     float nlo1 = 0.f, nhi1 = 0.f, n2l = 0.f, n2h = 0.f, n3l = 0.f, n3h = 0.f;
+    // the next element's D_Z^-1 row (a table in L2) moves to L1 meanwhile
+    if constexpr (!DZC)
+      if (nlive && !m.uniform) prefetch_l1(dinv_r + (long long)(e + 1) * (N2 * R) + R * line);
     if (nlive) {
       nlo1 = same ? xhi1 : ld(no.x1l);
       nhi1 = ld(no.x1h);
