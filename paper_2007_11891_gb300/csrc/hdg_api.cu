@@ -899,7 +899,9 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
   const int base = hdg::tpt_ppb(c->n);
   const int max_threads = prec == HDG_FP64 ? 320 : hdg::fast_max_threads(c->n);
   for (int pp : {base / 2, base - 1, base + 1, base * 3 / 2})
-    if (pp >= 1 && pp != base && hdg::tpt_threads(c->n, pp) <= max_threads) slots.push_back(pp);
+    if (pp >= 1 && pp != base &&
+        (prec == HDG_FP64 ? hdg::tpt_threads(c->n, pp) : hdg::fast_threads(c->n, pp)) <= max_threads)
+      slots.push_back(pp);
   const int keep_seg = c->seg_override, keep_ppb = c->ppb_override;
   cudaEvent_t e0, e1;
   HDG_CUDA(cudaEventCreate(&e0));

@@ -14,7 +14,7 @@ int fast_occupancy(int ppb) {
   static int cached[65] = {0};
   const int key = ppb < 64 ? ppb : 64;
   if (cached[key] > 0) return cached[key];
-  const int threads = tpt_threads(N, ppb);
+  const int threads = fast_threads(N, ppb);
   const size_t smem = (size_t)ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
   if (smem > kSmemOptIn)
     cudaFuncSetAttribute(tpt_fast_kernel<N, DZC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -34,9 +34,9 @@ cudaError_t fast_launch(const TptArgs<float, ST>& a, int nrhs, cudaStream_t s) {
   const long long nelem = a.npencils * a.mesh.ne[0];
   if (nelem <= 0) return cudaSuccess;
   if (a.chunk < 1 || a.ppb < 1) return cudaErrorInvalidValue;
-  const int threads = tpt_threads(N, a.ppb);
+  const int threads = fast_threads(N, a.ppb);
   const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
-  if (threads > fast_max_threads(N)) return cudaErrorInvalidConfiguration;
+  if (threads > fast_max_threads(N) || (fast_aligned(N) && a.ppb > 15)) return cudaErrorInvalidConfiguration;
   if (smem > kSmemOptIn) {
     cudaError_t e = cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, ST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

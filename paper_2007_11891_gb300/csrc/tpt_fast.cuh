@@ -55,12 +55,19 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   __shared__ CgScalars s_cg;
   const HookPre hpre = hook_prefetch(a.hook, rhs, &s_cg);
 
+  constexpr bool AL = fast_aligned(N);
+  constexpr int SLOT_T = fast_slot_threads(N);
   const int tid = threadIdx.x;
-  const int slot = tid / N2;
-  const int line = tid - slot * N2;
+  const int slot = tid / SLOT_T;
+  const int line = tid - slot * SLOT_T;   // >= N2 on the padding lanes of a whole-warp slot
   const int lo_i = line % N, hi_i = line / N;
   const int qpad = lo_i + R * hi_i;
-  const bool in_slot = slot < a.ppb;
+  const bool in_slot = slot < a.ppb && line < N2;
+  // barrier of this slot's threads (whole warps: a named barrier), else the CTA's
+  auto slot_sync = [&]() {
+    if constexpr (AL) asm volatile("bar.sync %0, %1;" ::"r"(1 + slot), "r"(SLOT_T) : "memory");
+    else __syncthreads();
+  };
   float* base = sm + (in_slot ? slot : 0) * PER;
   float* U = base + 8 * SF;
 
@@ -115,7 +122,7 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   bool have_carry = false;
   float dot = 0.f;
 
-  // same trip count in every slot of the CTA (the loop holds barriers)
+  // same trip count in every slot (the loop holds barriers)
   for (int t = 0; t < chunk; ++t) {
     const bool live = e < eend;
     float* S = base + (t & 1) * 4 * SF;
@@ -158,7 +165,7 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
     }
     const float4 mt = *reinterpret_cast<const float4*>(a.metric + (m.uniform ? 0 : 4 * (live ? e : 0)));
     const float d0 = mt.x, d1 = mt.y, d2 = mt.z, d3 = mt.w;
-    __syncthreads();
+    slot_sync();
 
     float Pp = 0.f, Pm = 0.f;
     if (live) {
@@ -199,7 +206,7 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
         *reinterpret_cast<float4*>(Ur + 4 * q) = make_float4(u[0], u[1], u[2], u[3]);
       });
     }
-    __syncthreads();
+    slot_sync();
 
     if (live) {
       const int i = lo_i, mm = hi_i;

@@ -213,11 +213,19 @@ __host__ __device__ constexpr int tpt_smem_per_pencil() {
   return 2 * 4 * N * dz_row(N, sizeof(T)) + N * N * dz_row(N, sizeof(T));
 }
 
-// FP32 apply kernel (tpt_fast.cuh): CTA size limit and guaranteed resident
-// CTAs per SM.  256 threads (256 / n^2 element slots) and three CTAs (at
-// most 80 registers) for n <= 16, which measured 16% faster than two CTAs
-// with more registers; n = 17 needs 289 threads per slot.
-__host__ __device__ constexpr int fast_max_threads(int n) { return n * n > 256 ? 320 : 256; }
+// FP32 apply kernel (tpt_fast.cuh): slot layout, CTA size limit and
+// guaranteed resident CTAs per SM.  Where rounding a slot up to whole warps
+// wastes few lanes (n = 8, 9 and n >= 11), every slot owns whole warps and
+// synchronises on its own named barrier, so a slow warp holds back only its
+// slot; otherwise (n <= 7, n = 10) slots are packed n^2 threads apart and
+// share the CTA barrier.  Up to 256 threads (288 for n = 9: three slots of
+// three warps) and three CTAs per SM (at most 80, for n = 9 72, registers)
+// for n <= 16, which measured 16% faster than two CTAs with more
+// registers; n = 17 needs 289 threads per slot.
+__host__ __device__ constexpr bool fast_aligned(int n) { return n >= 8 && n != 10; }
+__host__ __device__ constexpr int fast_slot_threads(int n) { return fast_aligned(n) ? (n * n + 31) / 32 * 32 : n * n; }
+__host__ __device__ constexpr int fast_threads(int n, int ppb) { return (ppb * fast_slot_threads(n) + 31) / 32 * 32; }
+__host__ __device__ constexpr int fast_max_threads(int n) { return n * n > 256 ? 320 : (n == 9 ? 288 : 256); }
 __host__ __device__ constexpr int fast_min_ctas(int n) { return n * n > 256 ? 2 : 3; }
 
 
