@@ -250,9 +250,11 @@ hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
  * of elements per CTA slot; slots and run length from hdg_set_slots_per_cta
  * and hdg_set_x1_segment), 2 x2-planes (one thread per x2-plane of an
  * element, n threads per element, elements_per_cta elements per CTA, 0 =
- * automatic).  Same arithmetic per point; results agree to FP32 rounding.
- * Errors: INVALID_ARG (NULL context, variant outside 0..2, or a plane CTA
- * above 128 threads).                                                      */
+ * automatic), 3 warp slots (one warp per element run, lane t owning the
+ * x1-lines t + 32 q, runs of hdg_set_x1_segment elements or automatic; no
+ * block barrier in the element loop).  Same arithmetic per point; results
+ * agree to FP32 rounding.  Errors: INVALID_ARG (NULL context, variant
+ * outside 0..3, or a plane CTA above 128 threads).                         */
 hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant, int elements_per_cta);
 
 /* Which kernel applies K in the nodal basis (hdg_apply with HDG_FP64 and

@@ -243,7 +243,7 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mod
   a.ppb = c->ppb_override > 0 ? c->ppb_override : hdg::tpt_ppb(c->n);
   a.npencils = (long long)c->mesh.ne[1] * c->mesh.ne[2];
   // persistent grid: one resident wave of CTAs, each CTA looping over slot groups
-  const int ctas = c->sms * hdg::tpt_blocks_per_sm<T, ST>(mode, c->n, a.ppb);
+  int ctas = c->sms * hdg::tpt_blocks_per_sm<T, ST>(mode, c->n, a.ppb);
   hdg::tpt_split(c->n, c->mesh.ne, nrhs, ctas, a.ppb, &a.seg, &a.nseg);
   if (c->seg_override > 0) {
     a.seg = std::min(c->seg_override, c->mesh.ne[0]);
@@ -254,8 +254,13 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mod
   // (the planes measured slower on the 16^3, p = 8 workload)
   if (std::is_same<ST, float>::value && mode == hdg::TPT_APPLY) {
     const int want = c->op_variant != 0 ? c->op_variant : 1;
-    a.variant = want == 2 ? 1 : 0;
+    a.variant = want == 2 ? 1 : (want == 3 ? 2 : 0);
     if (a.variant == 1) a.ppb = c->plane_epc > 0 ? c->plane_epc : std::max(1, 64 / c->n);
+    if (a.variant == 2) {   // one warp per slot: its own occupancy sets the resident wave
+      a.ppb = hdg::kWarpSlotsPerCta;
+      ctas = c->sms * hdg::warp_slots_blocks_per_sm(c->n);
+      a.max_grid = ctas;
+    }
   }
   // FP32 apply: equal contiguous runs, one per slot of a resident wave (per
   // right-hand side: the wave is shared by the batch)
@@ -957,8 +962,8 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
 }
 
 hdg_status hdg_set_operator_variant(hdg_ctx* c, int variant, int elements_per_cta) {
-  if (!c || variant < 0 || variant > 2 || elements_per_cta < 0 || elements_per_cta * c->n > 128)
-    return fail(HDG_ERR_INVALID_ARG, "NULL context, variant outside 0..2 or x2-plane CTA above 128 threads");
+  if (!c || variant < 0 || variant > 3 || elements_per_cta < 0 || elements_per_cta * c->n > 128)
+    return fail(HDG_ERR_INVALID_ARG, "NULL context, variant outside 0..3 or x2-plane CTA above 128 threads");
   c->op_variant = variant;
   c->plane_epc = elements_per_cta;
   return HDG_OK;

@@ -24,6 +24,10 @@ void tpt_split(int n, const int ne[3], int nrhs, int ctas, int ppb, int* seg, in
 // resident CTAs per SM of tpt_kernel<T, ST, n, mode> at ppb slots per CTA
 template <typename T, typename ST>
 int tpt_blocks_per_sm(int mode, int n, int ppb);
+// resident CTAs per SM of the FP32 warp-slot operator (tpt_warp.cuh), whose
+// CTAs hold kWarpSlotsPerCta one-warp slots
+constexpr int kWarpSlotsPerCta = 4;
+int warp_slots_blocks_per_sm(int n);
 
 // ---- tp_nodal.cu: nodal-basis operator in one kernel (Alg. hdg_op_3d) ------
 struct NodalArgs {

@@ -111,9 +111,10 @@ class HDG:
         _capi.check(_capi.lib().hdg_set_dz_mode(self._h, code), "hdg_set_dz_mode")
 
     def set_operator_variant(self, variant, elements_per_cta=0):
-        """FP32 operator tuning: 'auto', 'runs' (one thread per x1-line) or
-        'planes' (one thread per x2-plane; elements_per_cta, 0 = automatic)."""
-        code = {"auto": 0, "runs": 1, "planes": 2}[variant]
+        """FP32 operator tuning: 'auto', 'runs' (one thread per x1-line),
+        'planes' (one thread per x2-plane; elements_per_cta, 0 = automatic) or
+        'warps' (one warp per element slot)."""
+        code = {"auto": 0, "runs": 1, "planes": 2, "warps": 3}[variant]
         _capi.check(_capi.lib().hdg_set_operator_variant(self._h, code, int(elements_per_cta)),
                     "hdg_set_operator_variant")
 

@@ -210,13 +210,16 @@ def test_apply_bf16_storage(ne, bc, p, stretched):
         h.apply(x, 1.5, basis="nodal")
 
 
-@pytest.mark.parametrize("variant", ["runs", "planes"])
-@pytest.mark.parametrize("name,ne,bc,p,stretched,lam,tau", CASES[1:7], ids=[c[0] for c in CASES[1:7]])
+@pytest.mark.parametrize("variant", ["runs", "planes", "warps"])
+@pytest.mark.parametrize("name,ne,bc,p,stretched,lam,tau", CASES, ids=[c[0] for c in CASES])
 def test_apply_fp32_variants_match_oracle(variant, name, ne, bc, p, stretched, lam, tau):
-    # both FP32 work splits (one thread per x1-line in element runs, one
-    # thread per x2-plane) against the oracle, and bitwise repeatable
+    # the FP32 work splits (one thread per x1-line in element runs, one
+    # thread per x2-plane, one warp per element slot) against the oracle,
+    # and bitwise repeatable
     h, pr = _pair(ne, bc, p, stretched, lam, tau)
     h.set_operator_variant(variant)
+    if h.trace_size == 0:
+        return
     x = hdg_inputs.uniform_pm1(h.trace_size, 5)
     xt = torch.tensor(x, device="cuda", dtype=torch.float32)
     y = h.apply(xt, lam)
@@ -235,7 +238,7 @@ def test_planes_solve_matches_runs_solve():
     grid = _grid(ne, True, 31)
     f = torch.tensor(hdg_inputs.gaussian(6 * 5 * 4 * 7 ** 3, 31), device="cuda")
     out = {}
-    for variant in ("runs", "planes"):
+    for variant in ("runs", "planes", "warps"):
         h = HDG(ne, grid, (0,) * 6, p, 25.0)
         h.set_operator_variant(variant)
         tr, u, info = h.solve(f, lam, tol=1e-11, inner="fp32")
@@ -243,6 +246,20 @@ def test_planes_solve_matches_runs_solve():
         out[variant] = u
     ref = out["runs"].abs().max().item()
     assert (out["planes"] - out["runs"]).abs().max().item() <= 1e-8 * ref
+    assert (out["warps"] - out["runs"]).abs().max().item() <= 1e-8 * ref
+
+
+def test_warps_variant_full_size_matches_runs():
+    from paper_2007_11891_gb300 import HDG
+    cfg = hdg_inputs.WORKLOADS["stretched_p8"]
+    ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"]
+    h = HDG(ne, hdg_inputs.grid_lines(ne, cfg["stretched"]), (0,) * 6, p, hdg_inputs.TAU_HAT)
+    x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device="cuda", dtype=torch.float32)
+    y_runs = h.apply(x, lam, basis="transformed")
+    h.set_operator_variant("warps")
+    y_w = h.apply(x, lam, basis="transformed")
+    assert torch.equal(h.apply(x, lam, basis="transformed"), y_w)
+    assert float((y_w - y_runs).abs().max()) <= 1e-6 * float(y_runs.abs().max())
 
 
 # ---- nodal basis in one kernel (Alg. hdg_op_3d, HDG-TP) ------------------------
