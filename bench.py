@@ -40,7 +40,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # capture summarised in profiles/tpt_fast_kernel_fp32_cg_loop_stretched16_p8.md
 # (cold caches; the D_Z^-1 table of the stretched grid is most of the excess
 # over the 2 T x 4 B algorithmic bytes)
-TRAFFIC_BYTES = {"op_fp32": 22.76e6}
+TRAFFIC_BYTES = {"op_fp32": 22.75e6}
 
 
 def peaks():
