@@ -221,11 +221,12 @@ hdg_status hdg_solve_adjoint(hdg_ctx* ctx, int nrhs, const double* h_lambda, con
 hdg_status hdg_set_x1_segment(hdg_ctx* ctx, int elements);
 
 /* Tuning (not part of the method): number of element slots per CTA of the
- * element-run operator kernels (each slot is n^2 threads); 0 restores the
+ * element-run operator kernels (each slot is n^2 threads, rounded up to
+ * whole warps in the FP32 kernel for n = 8, 9 and n >= 11); 0 restores the
  * automatic choice.  Speed only.  Errors: INVALID_ARG (NULL context,
  * negative count, or a count whose CTA would exceed 320 threads); an FP32
- * apply whose CTA would exceed 256 threads (n <= 16) fails with CUDA
- * (invalid configuration).                                                 */
+ * apply whose CTA would exceed 256 threads (288 at n = 9; n <= 16) fails
+ * with CUDA (invalid configuration).                                        */
 hdg_status hdg_set_slots_per_cta(hdg_ctx* ctx, int slots);
 
 /* Autotuner (not part of the method): times the operator kernel of `prec`
