@@ -28,6 +28,9 @@ int tpt_blocks_per_sm(int mode, int n, int ppb);
 // CTAs hold kWarpSlotsPerCta one-warp slots
 constexpr int kWarpSlotsPerCta = 4;
 int warp_slots_blocks_per_sm(int n);
+// FP32 apply with the alternative work splits (hdg_set_operator_variant)
+cudaError_t launch_tpt_warp_slots(int n, const TptArgs<float, float>& a, int nrhs, cudaStream_t s);
+cudaError_t launch_tpt_planes(int n, const TptArgs<float, float>& a, int nrhs, cudaStream_t s);
 
 // ---- tp_nodal.cu: nodal-basis operator in one kernel (Alg. hdg_op_3d) ------
 struct NodalArgs {
