@@ -367,6 +367,9 @@ def run_sweep(args):
     stream = torch.cuda.current_stream()
 
     def per_launch_ms(fn, reps):
+        for _ in range(3):   # warm-up: first-use costs (module loading, attributes) stay out
+            fn()
+        torch.cuda.synchronize()
         tot = 0.0
         for _ in range(reps):
             flush.fill_(1.0)
