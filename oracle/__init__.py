@@ -29,9 +29,16 @@ linearly scaling operator", arXiv:2007.11891):
                    blocks of Tab. (hdg_matrices_threed) with one direction
                    fewer, global apply and a direct solve.
 
-It shares no code with the CUDA path: no eigen-decomposition, no
-sum factorisation, no fast diagonalisation.  Every pin it is checked against
+* ``facebasis`` -- the face eigenbasis that defines the library's
+                   transformed trace basis (Eq. (generalized_eigenvalue_
+                   decomposition) with the documented parity, order and sign
+                   convention), used only to express the dense K in that
+                   basis for comparisons: K-hat = T^T K T face by face.
+
+It shares no code with the CUDA path: its operator uses no
+eigen-decomposition, no sum factorisation and no fast diagonalisation
+(``facebasis`` changes the basis of the dense operator, nothing else).  Every pin it is checked against
 lives in ``tests/test_oracle_*.py``.
 """
 
-from . import basis1d, element3d, lowdim, mesh, solver  # noqa: F401
+from . import basis1d, element3d, facebasis, lowdim, mesh, solver  # noqa: F401
