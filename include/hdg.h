@@ -84,7 +84,15 @@ typedef enum { HDG_FP64 = 0, HDG_FP32 = 1, HDG_BF16 = 2 } hdg_precision;
  *     evaluated as in Alg. (hdg_op_3d)).
  *   HDG_BASIS_TRANSFORMED: coefficients in the face eigenbasis of
  *     Sec. 4.2, ut-hat = (S^T M (x) S^T M) ut per face, where the operator is
- *     K-hat = (S^T (x) S^T) K (S (x) S) of Alg. (hdg_op_3d_transformed).      */
+ *     K-hat = (S^T (x) S^T) K (S (x) S) of Alg. (hdg_op_3d_transformed).
+ *     S is fixed uniquely (for distinct eigenvalues) as follows: its columns
+ *     solve L s = Lambda M s with s^T M s = 1 (Eq. (generalized_eigenvalue_
+ *     decomposition), L = E + D M^-1 D^T); the GLL points are mirror
+ *     symmetric, so every column is even or odd under x -> -x; the columns
+ *     are ordered even modes first, then odd modes, each group by increasing
+ *     eigenvalue; and each column's sign makes B_S[m][0] > 0, with
+ *     B_S = S^T B - S^T D M^-1 C of Eq. (hdg_bs).  Face mode (m1, m2) of a
+ *     face is stored at m1 + n m2 (the face's lower axis fastest).          */
 typedef enum { HDG_BASIS_NODAL = 0, HDG_BASIS_TRANSFORMED = 1 } hdg_basis;
 
 typedef struct {
@@ -156,30 +164,36 @@ hdg_status hdg_apply(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_precisi
  * device memory.  The paper has no counterpart: this is an interface for
  * such callers, not part of the method.
  *
- * Who needs it: code that runs while the program is capturing a CUDA graph
- * (cudaMalloc and cudaFree are not allowed during capture, and cudaFree
- * synchronises the whole device), real-time loops that must neither
- * synchronise nor risk an allocation failure once running, and programs
- * whose device memory is owned by a pooling allocator that forbids
- * allocations made behind its back.  hdg_apply grows internal workspaces
- * with cudaMalloc the first time a size or lambda is seen; this entry point
- * never calls cudaMalloc, cudaFree or any allocating routine.
+ * Who needs it: real-time loops that must neither synchronise nor risk an
+ * allocation failure once running (cudaFree synchronises the whole device),
+ * programs whose device memory belongs to a pooling allocator that forbids
+ * allocations made behind its back, and code that must run within a device
+ * memory budget set at start-up.  hdg_apply grows internal workspaces with
+ * cudaMalloc the first time a size or lambda is seen; this entry point never
+ * calls cudaMalloc, cudaFree or any allocating routine.
  *
  * Its temporaries (the face-eigenbasis traces before and after the
  * operator, 2 x nrhs x hdg_trace_size() doubles, and the D_Z^-1 tables of
  * the lambdas, nrhs x n^2 x (n rounded up to even) doubles on a uniform
- * grid, n_e times that on a stretched one) live in one static device array of 2^21 doubles (16 MiB),
- * which every GPU that loads the library reserves until the process exits.
- * Larger requests are rejected with HDG_ERR_INVALID_ARG and a message
- * giving the size needed (use hdg_apply then).
+ * grid, n_e times that on a stretched one) live in one static device array
+ * of 2^21 doubles (16 MiB), which every GPU that loads the library reserves
+ * until the process exits.  Larger requests are rejected with
+ * HDG_ERR_INVALID_ARG and a message giving the size needed (use hdg_apply
+ * then).
  *
  * The first call on a device looks up that array's device address with
- * that device current; make that first call before any stream capture.
- * All calls share the one array, which keeps the previous call's contents:
- * calls whose work overlaps on the GPU (different streams, or different
- * host threads) race on it and must be serialised by the caller.
- * Arguments, layout and results are those of hdg_apply with FP64 nodal
- * traces; the current device must be the context's device.              */
+ * that device current (and may load the library's device code there); make
+ * that first call before any stream capture.  The address is cached per
+ * device for the life of the process: after cudaDeviceReset it is stale, so
+ * do not call this entry point again after a reset.  All calls share the one
+ * array, which keeps the previous call's contents (whatever must start at
+ * zero is cleared by each call): calls whose work overlaps on the GPU
+ * (different streams, or different host threads) race on it and must be
+ * serialised by the caller.  The operator's work split is always the
+ * automatic one (hdg_set_x1_segment and hdg_set_slots_per_cta are not
+ * consulted; every split gives bitwise the same result).  Arguments, layout
+ * and results are those of hdg_apply with FP64 nodal traces; the current
+ * device must be the context's device.                                    */
 hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_lambda, const double* d_x, double* d_y,
                             void* stream);
 

@@ -847,7 +847,12 @@ bool ctx_view(const hdg_ctx* c, CtxView* v) {
   v->nclass = nclass(c);
   return true;
 }
-void set_last_error(const char* msg) { g_last_error = msg; }
+void set_last_error(const char* msg) {
+  if (msg[0] == 0) g_last_error.clear();
+  else fail(HDG_OK, msg);   // quotes an error that was pending at entry, as every entry point does
+}
+void begin_entry() { begin_call(); }
+hdg_status check_lambdas(int nrhs, const double* lam) { return check_lambda(nullptr, nrhs, lam); }
 }  // namespace hdg
 
 // 1D / 2D context (hdg_lowdim_*): mesh bookkeeping, 1D tables, metric

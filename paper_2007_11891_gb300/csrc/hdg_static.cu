@@ -25,7 +25,10 @@ double* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the array on the current device.  Host code sees only a
 // host-side stand-in under the array's name, so the address is looked up
-// once per device with that device current.
+// once per device with that device current, on the first call there.  The
+// cached address belongs to that device's primary context: after
+// cudaDeviceReset (which destroys the context and every module in it) the
+// cache is stale, and this entry point must not be used again in the process.
 hdg_status scratch_address(int dev, double** out) {
   if (dev < 0 || dev >= kMaxDevices) {
     hdg::set_last_error("hdg_apply_static: device ordinal out of range");
@@ -45,13 +48,17 @@ hdg_status scratch_address(int dev, double** out) {
   return HDG_OK;
 }
 
+// Lambdas travel to the device as kernel parameters (8 KB per launch, within
+// the 32 KB parameter space of sm_70 and later), so no host buffer has to be
+// pinned and no copy engine is involved: at most 64 launches for the largest
+// batch of 65535 right-hand sides.
+constexpr int kLambdaChunk = 1024;
 struct LambdaChunk {
-  double v[32];
+  double v[kLambdaChunk];
 };
 
 __global__ void store_lambdas(double* dst, LambdaChunk c, int count) {
-  const int i = threadIdx.x;
-  if (i < count) dst[i] = c.v[i];
+  for (int i = threadIdx.x; i < count; i += blockDim.x) dst[i] = c.v[i];
 }
 
 long long round_up(long long v) { return (v + 31) / 32 * 32; }  // 256-byte multiples of doubles
@@ -65,17 +72,13 @@ hdg_status cuda_fail(cudaError_t e, const char* what) {
 
 extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_lambda, const double* d_x,
                                        double* d_y, void* stream) {
-  hdg::set_last_error("");
+  hdg::begin_entry();
   hdg::CtxView v;
   if (!hdg::ctx_view(ctx, &v) || !h_lambda || !d_x || !d_y || nrhs < 1 || nrhs > 65535) {
     hdg::set_last_error("hdg_apply_static: NULL pointer or nrhs outside 1..65535");
     return HDG_ERR_INVALID_ARG;
   }
-  for (int r = 0; r < nrhs; ++r)
-    if (!(h_lambda[r] >= 0.0) || !(h_lambda[r] < 1e308)) {
-      hdg::set_last_error("hdg_apply_static: lambda must be finite and >= 0");
-      return HDG_ERR_INVALID_ARG;
-    }
+  if (hdg_status ls = hdg::check_lambdas(nrhs, h_lambda); ls != HDG_OK) return ls;
   const long long dzt = (long long)v.n * v.n * hdg::dz_row(v.n, sizeof(double));   // one D_Z^-1 table
   const long long trace = round_up((long long)nrhs * v.ntrace);
   const long long table = round_up((long long)nrhs * v.nclass * dzt);
@@ -102,11 +105,11 @@ extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_l
   double* dinv = yh + trace;
   double* lam = dinv + table;
 
-  for (int r0 = 0; r0 < nrhs; r0 += 32) {
+  for (int r0 = 0; r0 < nrhs; r0 += kLambdaChunk) {
     LambdaChunk c{};
-    const int cnt = nrhs - r0 < 32 ? nrhs - r0 : 32;
+    const int cnt = nrhs - r0 < kLambdaChunk ? nrhs - r0 : kLambdaChunk;
     for (int i = 0; i < cnt; ++i) c.v[i] = h_lambda[r0 + i];
-    store_lambdas<<<1, 32, 0, s>>>(lam + r0, c, cnt);
+    store_lambdas<<<1, 256, 0, s>>>(lam + r0, c, cnt);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "store lambdas");
   if ((e = hdg::launch_dinv<double>(v.n, lam, nrhs, v.metric64, v.nclass, v.Lambda, dinv, s)) != cudaSuccess)

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/hdg.h"
+
 #include "common.cuh"
 #include "tpt_kernel.cuh"
 
@@ -157,4 +159,10 @@ struct hdg_ctx;
 namespace hdg {
 bool ctx_view(const hdg_ctx* c, CtxView* out);
 void set_last_error(const char* msg);
+// entry-point prologue of every C ABI call: clears the previous message and
+// takes a CUDA error left pending by earlier work out of the runtime's slot
+// (quoted in this call's message if it fails)
+void begin_entry();
+// lambda_r finite and >= 0 for r < nrhs (INVALID_ARG and a message otherwise)
+hdg_status check_lambdas(int nrhs, const double* lam);
 }  // namespace hdg

@@ -342,6 +342,14 @@ int build_setup1d(int p, double tau_hat, int mass_lumped, Setup1D* out, const ch
   for (int m = 0; m < n; ++m) {
     double b0 = 0.0, b1 = 0.0;
     for (int i = 0; i < n; ++i) { b0 += s.S[i * n + m] * v0[i]; b1 += s.S[i * n + m] * v1[i]; }
+    // sign convention of the face eigenbasis: every mode couples to the low
+    // face with B_S[m][0] > 0 (|B_S[m][0]| stays near pi/2 or above for every
+    // degree, so the sign is well defined, unlike an endpoint value of S)
+    if (b0 < 0.0) {
+      for (int i = 0; i < n; ++i) s.S[i * n + m] = -s.S[i * n + m];
+      b0 = -b0;
+      b1 = -b1;
+    }
     s.bs[m] = b0;
     double sigma = m < ne ? 1.0 : -1.0;
     s.err_parity = std::max(s.err_parity, std::fabs(b1 - sigma * b0));

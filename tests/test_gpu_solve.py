@@ -123,8 +123,12 @@ def test_singular_is_reported():
     assert ei.value.status == 2
 
 
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
 @pytest.mark.parametrize("ne,p", [((2, 2, 2), 2), ((4, 4, 4), 3)])
-def test_adjoint_matches_oracle(ne, p):
+def test_adjoint_matches_oracle(ne, p, inner):
+    # FP64 inner CG, and the mixed-precision path (FP32 inner CG inside FP64
+    # refinement) that the adjoint uses by default: both refine to a relative
+    # residual of 1e-13 in FP64, so both must match the oracle's dense adjoint
     from paper_2007_11891_gb300 import HDG
     lam = 5.0
     grid = hdg_inputs.grid_lines(ne)
@@ -134,11 +138,13 @@ def test_adjoint_matches_oracle(ne, p):
     f = hdg_inputs.gaussian(len(X), 11897)
     ut = hdg_inputs.smooth_target(X, hdg_inputs.smooth_target_coeffs())
     L, dLdf, dLdlam, u_ref = pr.adjoint(f, ut, method="direct")
-    _, u, _ = h.solve(torch.tensor(f, device="cuda"), lam, tol=1e-13, inner="fp64")
+    _, u, info_f = h.solve(torch.tensor(f, device="cuda"), lam, tol=1e-13, inner=inner)
     assert np.abs(u.cpu().numpy() - u_ref).max() <= 1e-9 * np.abs(u_ref).max()
-    gf, gl, info = h.solve_adjoint(u, 2.0 * (u - torch.tensor(ut, device="cuda")), lam, tol=1e-13, inner="fp64")
+    gf, gl, info = h.solve_adjoint(u, 2.0 * (u - torch.tensor(ut, device="cuda")), lam, tol=1e-13, inner=inner)
     assert np.abs(gf.cpu().numpy() - dLdf).max() <= 1e-8 * np.abs(dLdf).max()
     assert abs(float(gl[0]) - dLdlam) <= 1e-8 * abs(dLdlam)
+    if inner == "fp32":
+        assert info_f[0]["outer"] >= 2 and info[0]["outer"] >= 2   # refinement did the work
 
 
 def test_autograd_function():
