@@ -7,8 +7,12 @@ inside FP64 iterative refinement to ||F - K ut|| <= 1e-10 ||F|| (nodal
 basis), traces back-transformed, u recovered.  L2 is flushed (a 256 MB
 write) before every timed step.
 
-value = trace DOFs x condensed-operator applications per step / step time
-(GDOF/s), summed over ranks.  Each rank solves its own replica (different
+value = trace DOFs solved per second (GDOF/s): the trace unknowns of the
+problem divided by the time of one complete solve to 1e-10, summed over
+ranks.  It does not grow with the number of operator applications a solve
+needs; the operator's own rate (trace DOFs / operator launch time, live in
+the solve and isolated) and trace DOFs x applications / solve time are
+reported as secondary keys.  Each rank solves its own replica (different
 seed): the mesh is not partitioned across GPUs ("scaling": "weak").
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -32,15 +36,14 @@ import hdg_inputs  # noqa: E402
 METRIC = "condensed-operator GDOF/s + CG solve time to 1e-10, mixed vs FP64 on 1 GB300"
 WORKLOAD = "stretched_p8"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
-# FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2 flops x 2070 MHz (recipe's unit
-# counts and maximum clock); measured 1.19 TFLOP/s at 1987 MHz with an FMA loop
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
-# DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
-# capture summarised in profiles/tpt_fast_kernel_fp32_cg_loop_stretched16_p8.md
-# (cold caches; the D_Z^-1 table of the stretched grid is most of the excess
-# over the 2 T x 4 B algorithmic bytes)
-TRAFFIC_BYTES = {"op_fp32": 22.75e6}
+# FP64 FMA pipe derived from unit counts: 2 DFMA/clk/SM x 152 SMs x 2 flops x
+# 2070 MHz; the bench measures the rate itself (hdg_measure_fma_peak, an FMA
+# loop on every SM) and uses the measured value, this one only if that fails
+FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12
+# DRAM bytes (read + write) per launch of the dominant kernel from one ncu
+# capture of the same kernel and workload (cold caches); None when the
+# kernel changed after the capture
+TRAFFIC_BYTES = {"op_fp32": None}
 
 
 def peaks():
@@ -162,6 +165,22 @@ def job_step_ms(ms_step, world, device):
     return float(t[0])
 
 
+def solve_value(world, trace_dofs, ms_step):
+    """Whole-job GDOF/s solved: every rank solves its own replica of
+    `trace_dofs` unknowns to the tolerance within the job's step time."""
+    return world * trace_dofs / (ms_step * 1e-3) / 1e9
+
+
+def fp64_peak_tflops():
+    """(FP64 FMA rate in TFLOP/s, where it comes from): measured on this GPU by
+    the library's FMA loop, else derived from the unit counts."""
+    try:
+        from paper_2007_11891_gb300 import measure_fma_peak
+        return measure_fma_peak("fp64"), "measured: FP64 FMA loop on every SM (hdg_measure_fma_peak)"
+    except Exception:  # measurement unavailable: the unit-count figure
+        return FP64_PEAK_TFLOPS_DERIVED, "derived: 2 DFMA/clk/SM x 152 SMs at 2070 MHz"
+
+
 def job_value(world, trace_dofs, applies, ms_step):
     """Whole-job GDOF/s: every rank applies the operator `applies` times to
     its own replica's trace DOFs within the job's step time."""
@@ -223,7 +242,6 @@ def run_ours(args, rank, world, local_rank):
     clocks = clk.stop()
     applies = infos[0]["applies"]
     ms_step = job_step_ms(ms / args.steps, world, dev)
-    value = job_value(world, T, applies, ms_step)
 
     # FP64 solve with the same machinery (FP64 inner CG)
     solve_fp64()
@@ -272,8 +290,16 @@ def run_ours(args, rank, world, local_rank):
     h.profile(False)
     dominant = max(classes, key=lambda k: classes[k]["ms"])
     pk, src = peaks()
+    fp64_peak, fp64_src = fp64_peak_tflops()
     n = p + 1
     ne_tot = ne[0] * ne[1] * ne[2]
+    faces = T // (n * n)
+
+    def alu(kind, name, flops, avg_s, note):
+        ach = flops / avg_s / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": None, "peak_source": fp64_src, "avg_launch_us": avg_s * 1e6,
+                "algorithmic_flops_per_launch": flops, "flops_counted": note}
 
     def roof(kind):
         c = classes[kind]
@@ -281,57 +307,62 @@ def run_ours(args, rank, world, local_rank):
         if kind == "op_fp32":
             byts = 2.0 * T * 4
             ach = byts / avg_s / 1e9
-            return {"kernel": "tpt_fast_kernel<float> (operator, FP32)", "bound": "hbm", "achieved": ach,
+            return {"kernel": "tpt_tile_kernel<float> (operator, FP32, CG loop)", "bound": "hbm", "achieved": ach,
                     "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
-                    "traffic": TRAFFIC_BYTES["op_fp32"],
-                    "peak_source": "of " + src, "avg_launch_us": avg_s * 1e6,
-                    "algorithmic_bytes_per_launch": byts}
+                    "traffic": TRAFFIC_BYTES["op_fp32"], "peak_source": "of " + src, "avg_launch_us": avg_s * 1e6,
+                    "algorithmic_bytes_per_launch": byts,
+                    "bytes_counted": "read x + write y = 2 T x 4 B; D_Z^-1 is computed in the kernel on this "
+                                     "stretched grid (0 table bytes)",
+                    "algorithmic_bytes_with_stored_dz_table": byts + 4.0 * n ** 3 * ne_tot,
+                    "frac_with_stored_dz_table": (byts + 4.0 * n ** 3 * ne_tot) / avg_s / 1e9 / pk["hbm_gbs"]}
         if kind == "op_fp64":
-            flops = (12.0 * n ** 3 + 24.0 * n ** 2) * ne_tot
-            ach = flops / avg_s / 1e12
-            return {"kernel": "tpt_kernel<double> (operator, FP64)", "bound": "alu", "achieved": ach,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs at 2070 MHz", "avg_launch_us": avg_s * 1e6,
-                    "algorithmic_flops_per_launch": flops}
-        if kind in ("face", "volume", "rhs_recover"):
-            if kind == "face":
-                flops = 4.0 * n ** 3 * (T // (n * n))
-            elif kind == "volume":
-                flops = 6.0 * n ** 4 * ne_tot
-            else:
-                flops = (12.0 * n ** 3 + 24.0 * n ** 2) * ne_tot
-            ach = flops / avg_s / 1e12
-            return {"kernel": kind + " (FP64)", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs at 2070 MHz", "avg_launch_us": avg_s * 1e6,
-                    "algorithmic_flops_per_launch": flops}
-        byts = 7.0 * T * 4
+            return alu(kind, "tpt_tile_kernel<double> (operator, FP64, refinement residual)",
+                       (12.0 * n ** 3 + 24.0 * n ** 2) * ne_tot, avg_s,
+                       "executed: 12 n^3 + 24 n^2 per element (parity-split expansion and contraction)")
+        if kind == "face":
+            return alu(kind, "face_rows_kernel (FP64 face transforms)", 2.0 * n ** 3 * faces, avg_s,
+                       "executed: 2 n^3 per face (parity-split line transforms, rows and columns)")
+        if kind == "volume":
+            return alu(kind, "volume_transform_kernel (FP64)", 3.0 * n ** 4 * ne_tot, avg_s,
+                       "executed: 3 n^4 per element (parity-split line transforms along three directions)")
+        if kind == "rhs_recover":
+            return alu(kind, "tpt_kernel<double> RHS / RECOVER modes", (13.0 * n ** 3 + 24.0 * n ** 2) * ne_tot,
+                       avg_s, "executed: 13 n^3 + 24 n^2 per element")
+        byts = 13.0 * T * 4
         ach = byts / avg_s / 1e9
-        return {"kernel": "CG vector kernels", "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / pk["hbm_gbs"], "traffic": None, "peak_source": "of " + src,
-                "avg_launch_us": avg_s * 1e6}
+        return {"kernel": "CG vector kernels (cg_step_kernel<float> and the solve's other vector launches)",
+                "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                "traffic": None, "peak_source": "of " + src, "avg_launch_us": avg_s * 1e6,
+                "bytes_counted": "13 streams of T FP32 values per launch (cg_step_kernel reads u, w, p, s, x, r, W "
+                                 "and writes p, s, x, r, u, w); the average includes the few other vector launches"}
 
     roofline = roof(dominant)
     roofline["share_of_solve"] = classes[dominant]["ms"] / sum(c["ms"] for c in classes.values())
     others = {k: roof(k) for k in classes if k != dominant}
+    op_live = classes.get("op_fp32")
 
     line = {
-        "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "metric": METRIC, "value": solve_value(world, T, ms_step), "unit": "GDOF/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": "%s: 16x16x16 stretched grid (widths U[0.5,2], seeded), p=8, lambda=10, "
                                "tau_hat=25, Dirichlet, f~N(0,1); one full mixed-precision solve per step "
                                "(FP32 transformed CG inside FP64 refinement) to 1e-10" % WORKLOAD,
+                   "value": "trace DOFs / time of one solve to 1e-10 (summed over ranks)",
                    "trace_dofs": T, "volume_dofs": V, "l2": "flushed before each step (256 MB write)",
                    "parallelism": "replicas (one independent solve per GPU)"},
         "clocks": clocks,
-        "e2e": {"value": job_value(world, T, applies, ms_e2e), "unit": "GDOF/s",
+        "e2e": {"value": solve_value(world, T, ms_e2e), "unit": "GDOF/s",
                 "h2d_bytes_per_step": V * 8, "d2h_bytes_per_step": (V + T) * 8, "ms_per_step": ms_e2e},
         "gpu_launches": launches_per_solve * args.steps,
         "roofline": roofline,
         "roofline_other_kernels": others,
         "solve": {"mixed_ms": ms_step, "fp64_ms": ms64, "speedup_mixed_vs_fp64": ms64 / ms_step,
                   "mixed": infos[0], "fp64": infos64[0], "wall_s_timed": wall},
+        "operator_gdofs": {
+            "live_fp32_in_solve": (T / (op_live["ms"] / op_live["launches"] * 1e-3) / 1e9) if op_live else None,
+            "isolated_fp32": app["fp32"]["gdofs"], "isolated_fp64": app["fp64"]["gdofs"],
+            "applications_x_trace_dofs_per_solve_time": job_value(world, T, applies, ms_step)},
         "apply_isolated_transformed": app,
         "kernel_time_by_class_ms": classes,
     }
@@ -382,6 +413,15 @@ def run_sweep(args):
         return tot / reps
 
     parts = set(args.parts.split(","))
+    fp64_peak, fp64_src = fp64_peak_tflops()
+    fp32_peak = None
+    try:
+        from paper_2007_11891_gb300 import measure_fma_peak
+        fp32_peak = measure_fma_peak("fp32")
+    except Exception:  # measurement unavailable
+        pass
+    print(json.dumps({"sweep": "peaks", "fp64_tflops": fp64_peak, "fp64_source": fp64_src,
+                      "fp32_fma_loop_tflops": fp32_peak, "hbm_gbs": pk["hbm_gbs"], "hbm_source": src}), flush=True)
     if "operator" in parts:
         cfg = hdg_inputs.WORKLOADS["uniform32"]
         ne = cfg["ne"]
@@ -404,8 +444,8 @@ def run_sweep(args):
                 else:
                     flops = (12.0 * n ** 3 + 24.0 * n ** 2) * ne[0] * ne[1] * ne[2]
                     ach = flops / (ms * 1e-3) / 1e12
-                    line["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                        "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "derived FP64 pipe"}
+                    line["roofline"] = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                                        "frac": ach / fp64_peak, "peak_source": fp64_src}
                 print(json.dumps(line), flush=True)
             h.close()
             del x64
@@ -423,7 +463,11 @@ def run_sweep(args):
             nel = ne[0] * ne[1] * ne[2]
             x = torch.tensor(hdg_inputs.uniform_pm1(T, 11893), device=dev)
             y = torch.empty_like(x)
-            for variant, fl in (("facewise", 36.0 * n ** 3 + 24.0 * n ** 2), ("fused", 60.0 * n ** 3 + 24.0 * n ** 2)):
+            # executed flops per element: face-wise = parity-split face transforms
+            # in and out (2 n^3 each, three faces per element) around the
+            # transformed core (12 n^3 + 24 n^2); one kernel = dense transforms
+            # of all six faces in and out (48 n^3) around the same core
+            for variant, fl in (("facewise", 24.0 * n ** 3 + 24.0 * n ** 2), ("fused", 60.0 * n ** 3 + 24.0 * n ** 2)):
                 h.set_nodal_variant(variant)
                 h.apply(x, cfg["lam"], basis="nodal", out=y)
                 ms = per_launch_ms(lambda: h.apply(x, cfg["lam"], basis="nodal", out=y), 5)
@@ -431,9 +475,9 @@ def run_sweep(args):
                 print(json.dumps({"sweep": "nodal_apply", "workload": "uniform32", "p": p, "variant": variant,
                                   "trace_dofs": T, "us_per_apply": ms * 1e3, "gdofs": T / (ms * 1e-3) / 1e9,
                                   "flops_per_element": fl,
-                                  "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                                               "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                                               "peak_source": "derived FP64 pipe"}}), flush=True)
+                                  "roofline": {"bound": "alu", "achieved": ach, "peak": fp64_peak,
+                                               "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                                               "peak_source": fp64_src}}), flush=True)
             h.close()
             del x, y
     if "lowdim" in parts:

@@ -224,14 +224,17 @@ hdg_status hdg_solve_adjoint(hdg_ctx* ctx, int nrhs, const double* h_lambda, con
                              const double* d_grad_u, double* d_grad_f, double* d_grad_lambda,
                              const hdg_solve_opts* opts, hdg_solve_info* h_info, void* stream);
 
-/* Tuning (not part of the method): the number of elements one CTA slot of
- * the operator kernel marches over along x1.  FP64 kernels: a segment of
- * one x1-pencil; FP32 apply kernel: a contiguous run in element order that
- * may continue into the next pencil.  The x1-face between consecutive
- * elements of a slot is summed in registers, other shared faces with two
- * atomic adds onto zero.  0 restores the automatic choice (one resident
- * wave of slots covers the mesh).  Speed only: every value gives bitwise
- * identical results.  Errors: INVALID_ARG (NULL context, negative length). */
+/* Tuning (not part of the method): elements per unit of work of the
+ * operator kernel.  Element-tile kernel (the default): elements per tile,
+ * rounded up to a multiple of the CTA's element groups and reduced to what
+ * fits in shared memory; an x1-face between two elements of a tile is summed
+ * in shared memory.  Element-run kernels: the elements one CTA slot marches
+ * over along x1 (FP64: a segment of one x1-pencil; FP32: a contiguous run in
+ * element order that may continue into the next pencil), the x1-face
+ * between consecutive elements summed in registers.  Other shared faces take
+ * two atomic adds onto zero.  0 restores the automatic choice.  Speed only:
+ * every value gives bitwise identical results.  Errors: INVALID_ARG (NULL
+ * context, negative length).                                              */
 hdg_status hdg_set_x1_segment(hdg_ctx* ctx, int elements);
 
 /* Tuning (not part of the method): number of element slots per CTA of the
@@ -254,23 +257,38 @@ hdg_status hdg_autotune(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_prec
                         int* h_best_slots, double* h_best_us, void* stream);
 
 /* Tuning (not part of the method): where the FP32 operator takes the
- * inverse eigenvalue scaling D_Z^-1 of Sec. 4.1 from.  0 automatic (a table
- * when it fits in L2, else computed in the kernel), 1 always the table,
- * 2 always computed in the kernel (FP32 only; FP64 always uses the table).
- * Results agree to FP32 rounding.  Errors: INVALID_ARG.                    */
+ * inverse eigenvalue scaling D_Z^-1 of Sec. 4.1 from.  0 automatic (uniform
+ * grid: the one element class's table; stretched grid: computed in the
+ * kernel with the hardware reciprocal), 1 always a table (one per element on
+ * a stretched grid), 2 always computed in the kernel (FP32 only; FP64 always
+ * uses tables).  Results agree to FP32 rounding.  Errors: INVALID_ARG.     */
 hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
 
-/* Tuning (not part of the method): work split of the FP32 operator kernel.
- * 0 automatic (element runs), 1 element runs (one thread per x1-line, runs
- * of elements per CTA slot; slots and run length from hdg_set_slots_per_cta
- * and hdg_set_x1_segment), 2 x2-planes (one thread per x2-plane of an
- * element, n threads per element, elements_per_cta elements per CTA, 0 =
- * automatic), 3 warp slots (one warp per element run, lane t owning the
- * x1-lines t + 32 q, runs of hdg_set_x1_segment elements or automatic; no
- * block barrier in the element loop).  Same arithmetic per point; results
- * agree to FP32 rounding.  Errors: INVALID_ARG (NULL context, variant
- * outside 0..3, or a plane CTA above 128 threads).                         */
+/* Tuning (not part of the method): work split of the operator kernel.
+ * 0 automatic (element tiles), 4 element tiles (every precision: CTAs of
+ * n^2 G threads take tiles of consecutive elements; hdg_set_x1_segment sets
+ * the elements per tile, rounded to a multiple of G), 1 element runs (one
+ * thread per x1-line, runs of elements per CTA slot; slots and run length
+ * from hdg_set_slots_per_cta and hdg_set_x1_segment; FP64, FP32 and BF16),
+ * and for FP32 only 2 x2-planes (one thread per x2-plane of an element, n
+ * threads per element, elements_per_cta elements per CTA, 0 = automatic)
+ * and 3 warp slots (one warp per element run, lane t owning the x1-lines
+ * t + 32 q).  Same arithmetic per point; FP64 results are bitwise equal,
+ * FP32 results agree to FP32 rounding.  Errors: INVALID_ARG (NULL context,
+ * variant outside 0..4, or a plane CTA above 128 threads).                 */
 hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant, int elements_per_cta);
+
+/* Tuning (not part of the method): how an inner CG iteration runs.
+ *   0 (default) one kernel per iteration when the operator kernel is the
+ *     element-tile kernel (hdg_set_operator_variant 0 or 4): the launch of
+ *     iteration i + 1 applies the CG update of iteration i to every face
+ *     value it reads (each face value's one owner stores the new x, p, r, s)
+ *     and applies the operator to the new search direction; the two inner
+ *     products of the single-reduction CG are summed in the same launch;
+ *   1 two kernels per iteration: the operator, then the vector update.
+ * Both compute the same CG iterates in exact arithmetic.
+ * Errors: INVALID_ARG (NULL context, variant outside 0..1).               */
+hdg_status hdg_set_cg_variant(hdg_ctx* ctx, int variant);
 
 /* Which kernel applies K in the nodal basis (hdg_apply with HDG_FP64 and
  * HDG_BASIS_NODAL):
@@ -299,6 +317,14 @@ hdg_status hdg_set_nodal_variant(hdg_ctx* ctx, int variant);
  * whether or not recording is on; time is then 0).                         */
 hdg_status hdg_profile(hdg_ctx* ctx, int enable);
 hdg_status hdg_profile_read(hdg_ctx* ctx, int kernel_class, double* total_ms, long long* launches);
+
+/* Measurement support (not part of the method): the fused multiply-add
+ * rate of the current device in TFLOP/s (2 flops per FMA), measured with CUDA
+ * events over 5 launches (after one warm-up launch) of a kernel in which
+ * every thread runs 8 independent register-resident FMA chains, 4 blocks of
+ * 256 threads per SM.  prec: HDG_FP64 or HDG_FP32.  Synchronises the
+ * stream.  Errors: INVALID_ARG, CUDA.                                     */
+hdg_status hdg_measure_fma_peak(hdg_precision prec, double* h_tflops, void* stream);
 
 /* Message of the last failed call on this host thread ("" if none).      */
 const char* hdg_last_error(void);

@@ -4,4 +4,4 @@ The compute path is the in-tree CUDA library ``lib/libhdg_gb300.so``
 (sm_103a) behind the C ABI of ``include/hdg.h``; this package only marshals
 arguments (``_capi``) and wraps torch tensors (``hdg``).
 """
-from .hdg import HDG, HDGLowDim, HDGSolve  # noqa: F401
+from .hdg import HDG, HDGLowDim, HDGSolve, measure_fma_peak  # noqa: F401

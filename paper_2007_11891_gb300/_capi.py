@@ -19,7 +19,7 @@ EXPORTED = ["hdg_setup", "hdg_destroy", "hdg_trace_size", "hdg_volume_size", "hd
             "hdg_status_string", "hdg_profile", "hdg_profile_read", "hdg_set_x1_segment", "hdg_set_dz_mode",
             "hdg_set_slots_per_cta", "hdg_autotune", "hdg_set_operator_variant",
             "hdg_set_nodal_variant", "hdg_lowdim_setup", "hdg_lowdim_trace_size", "hdg_lowdim_apply",
-            "hdg_lowdim_destroy"]
+            "hdg_lowdim_destroy", "hdg_measure_fma_peak", "hdg_set_cg_variant"]
 
 
 class HdgLowDimMesh(ctypes.Structure):
@@ -96,6 +96,8 @@ def lib():
     L.hdg_set_dz_mode.restype = ci
     L.hdg_set_operator_variant.argtypes = [vp, ci, ci]
     L.hdg_set_operator_variant.restype = ci
+    L.hdg_set_cg_variant.argtypes = [vp, ci]
+    L.hdg_set_cg_variant.restype = ci
     L.hdg_set_nodal_variant.argtypes = [vp, ci]
     L.hdg_set_nodal_variant.restype = ci
     L.hdg_lowdim_setup.argtypes = [ctypes.POINTER(HdgLowDimMesh), ci, ctypes.POINTER(HdgOptions),
@@ -113,6 +115,8 @@ def lib():
     L.hdg_profile.restype = ci
     L.hdg_profile_read.argtypes = [vp, ci, pd, ctypes.POINTER(ctypes.c_longlong)]
     L.hdg_profile_read.restype = ci
+    L.hdg_measure_fma_peak.argtypes = [ci, pd, vp]
+    L.hdg_measure_fma_peak.restype = ci
     L.hdg_last_error.argtypes = []
     L.hdg_last_error.restype = ctypes.c_char_p
     L.hdg_status_string.argtypes = [ci]

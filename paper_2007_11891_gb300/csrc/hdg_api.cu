@@ -105,17 +105,22 @@ struct hdg_ctx {
   DevBuf loopctl;   // device loop-trip counter of the CG loop graph
   int seg_override = 0;   // x1 segment length; 0 = automatic
   int ppb_override = 0;   // slots per CTA; 0 = automatic
-  int op_variant = 0;     // FP32 apply kernel: 0 automatic, 1 element runs, 2 x2-planes
+  int op_variant = 0;     // apply kernel: 0 automatic (tiles), 1 element runs, 2 x2-planes, 3 warp slots, 4 tiles
   int nodal_variant = 0;  // FP64 nodal apply: 0 face-wise transforms + transformed kernel, 1 one kernel (HDG-TP)
   int plane_epc = 0;      // x2-plane kernel: elements per CTA; 0 = automatic
   int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
+  int fused_cg = 0;       // the current inner CG runs the fused tile-kernel step
+  int fused_enabled = 1;  // allow the fused step (hdg_set_cg_variant)
 };
 
 namespace {
 
 enum Ws {
   W_XHAT = 0, W_YHAT, W_FHAT_T, W_RHAT, W_TMP, W_FVOL, W_GHAT, W_WVOL,
-  W_R, W_D, W_P, W_Q, W_DOT, W_DOT2, W_U, W_S
+  W_R, W_D, W_P, W_Q, W_DOT, W_DOT2, W_U, W_S,
+  // fused CG step (tile kernel): second r and s buffers, second and third w
+  // buffers, per-block gamma partials
+  W_R2, W_S2, W_W2, W_W3, W_GP
 };
 
 hdg_status ensure(DevBuf& b, size_t bytes) {
@@ -184,12 +189,12 @@ long long nclass(const hdg_ctx* c) { return c->uniform ? 1 : c->nelem; }
 template <typename T>
 long long dz_table(const hdg_ctx* c) { return (long long)c->n * c->n * hdg::dz_row(c->n, sizeof(T)); }
 
-// D_Z^-1 is computed inside the FP32 operator kernel on stretched grids whose
-// per-element table would not stay resident in L2 next to the CG vectors
-// (beyond 24 MB the table costs more HBM traffic than the traces); FP64
-// kernels (bound by the FP64 pipe, where a division costs more than a load),
-// uniform grids (one small table) and small stretched grids read tables.
-constexpr size_t kDzTableL2Bytes = 24u << 20;
+// D_Z^-1 is computed inside the FP32 operator kernel on stretched grids (one
+// table per element would be n^3 values per element, more bytes than the
+// element's share of the traces, for a reciprocal the SFU computes at no
+// measurable cost); FP64 kernels (bound by the FP64 pipe, where a division
+// costs more than a load) and uniform grids (one small table, held in
+// shared memory) read tables.
 template <typename T>
 bool dz_in_kernel(const hdg_ctx* c) {
   if (sizeof(T) != 4) return false;
@@ -197,7 +202,7 @@ bool dz_in_kernel(const hdg_ctx* c) {
   if ((size_t)nclass(c) * dz_table<T>(c) >= (size_t(1) << 31)) return true;
   if (c->dz_mode == 1) return false;
   if (c->dz_mode == 2) return true;
-  return !c->uniform && (size_t)nclass(c) * dz_table<T>(c) * sizeof(T) > kDzTableL2Bytes;
+  return !c->uniform;
 }
 
 // lambdas on the device, per precision (kept while they do not change)
@@ -250,10 +255,13 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mod
     a.nseg = (c->mesh.ne[0] + a.seg - 1) / a.seg;
   }
   a.max_grid = ctas;
-  // FP32 apply kernel variant: element runs unless x2-planes are asked for
-  // (the planes measured slower on the 16^3, p = 8 workload)
-  if (std::is_same<ST, float>::value && mode == hdg::TPT_APPLY) {
-    const int want = c->op_variant != 0 ? c->op_variant : 1;
+  a.sms = c->sms;
+  a.tile = c->seg_override;   // elements per tile of the tile kernel (0 = automatic)
+  // apply kernel: element tiles (tpt_tile.cuh) unless another work split is
+  // asked for; the FP64 and BF16 applies have the tiles and the element runs
+  if (mode == hdg::TPT_APPLY && (c->op_variant == 0 || c->op_variant == 4)) a.variant = 3;
+  if (std::is_same<ST, float>::value && mode == hdg::TPT_APPLY && c->op_variant >= 1 && c->op_variant <= 3) {
+    const int want = c->op_variant;
     a.variant = want == 2 ? 1 : (want == 3 ? 2 : 0);
     if (a.variant == 1) a.ppb = c->plane_epc > 0 ? c->plane_epc : std::max(1, 64 / c->n);
     if (a.variant == 2) {   // one warp per slot: its own occupancy sets the resident wave
@@ -288,7 +296,7 @@ hdg_status tpt_apply(hdg_ctx* c, int nrhs, const T* dinv, const ST* x, ST* y, cu
                      bool pdl = false) {
   hdg::TptArgs<T, ST> a = base_args<T, ST>(c, dinv, nrhs);
   // the FP32 kernel's runs may split any x1-pencil: zero the whole output
-  if (!zeroed) HDG_TRY(zero_for_tpt<ST>(c, y, nrhs, sizeof(T) == 4 ? 2 : a.nseg, s));
+  if (!zeroed) HDG_TRY(zero_for_tpt<ST>(c, y, nrhs, (sizeof(T) == 4 || a.variant == 3) ? 2 : a.nseg, s));
   a.x = x;
   a.y = y;
   a.skip = skip;
@@ -415,9 +423,54 @@ __global__ void cg_loop_cond(cudaGraphConditionalHandle h, const hdg::CgScalars*
 // `count` CG iterations, two kernels each: the operator w = K-hat u with the
 // fused u^T w, then the single-reduction CG step (launch_cg_step).  Vectors:
 // x (d), r, u = W r, w (q), p, s = K-hat p.
+// `count` iterations of the fused CG step, one tile-kernel launch each
+// (tpt_tile.cuh, CgVecs): launch j applies the update of iteration j - 1 to
+// the face values it stages and applies the operator to u_j.  Buffers rotate
+// with j: r and s with period 2, w with period 3, so every sequence of
+// launches (eager or captured) starts at a multiple of kFusedPeriod.
+constexpr int kFusedPeriod = 6;
+template <typename T>
+hdg_status cg_fused_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* Wt, int count, cudaStream_t s) {
+  int* flags = static_cast<int*>(c->flags.p);
+  hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
+  double* uw = static_cast<double*>(c->scal.p) + nrhs;
+  hdg::CgHook hook{static_cast<double*>(c->partials.p), static_cast<unsigned int*>(c->counters.p), uw, cg, flags,
+                   nullptr, 0};
+  T* R[2] = {wsp<T>(c, W_R), wsp<T>(c, W_R2)};
+  T* S[2] = {wsp<T>(c, W_S), wsp<T>(c, W_S2)};
+  T* Wb[3] = {wsp<T>(c, W_Q), wsp<T>(c, W_W2), wsp<T>(c, W_W3)};
+  hdg::TptArgs<T, T> a = base_args<T, T>(c, dinv, nrhs);
+  a.variant = 3;
+  a.cg = 1;
+  a.skip = flags;
+  a.hook = hook;
+  a.pdl = c->pdl ? 1 : 0;
+  a.cgv.x = wsp<T>(c, W_D);
+  a.cgv.p = wsp<T>(c, W_P);
+  a.cgv.W = Wt;
+  a.cgv.gpartials = wsp<double>(c, W_GP);
+  for (int k = 0; k < count; ++k) {
+    a.cgv.r_in = R[k % 2];
+    a.cgv.r_out = R[(k + 1) % 2];
+    a.cgv.s_in = S[k % 2];
+    a.cgv.s_out = S[(k + 1) % 2];
+    a.cgv.w_in = Wb[k % 3];
+    a.y = Wb[(k + 1) % 3];
+    a.cgv.w_zero = Wb[(k + 2) % 3];
+    a.x = nullptr;
+    Timed t(c, sizeof(T) == 8 ? K_OP64 : K_OP32, s);
+    const cudaError_t e = hdg::launch_tpt<T, T>(hdg::TPT_APPLY, c->n, a, nrhs, s);
+    if (e != cudaSuccess)
+      return fail(HDG_ERR_CUDA, std::string("fused CG step launch (n=") + std::to_string(c->n) +
+                                    ", nrhs=" + std::to_string(nrhs) + "): " + cudaGetErrorString(e));
+  }
+  return HDG_OK;
+}
+
 template <typename T>
 hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, int count,
                          cudaStream_t s) {
+  if (c->fused_cg) return cg_fused_iterations<T>(c, nrhs, dinv, w, count, s);
   const long long T_ = c->ntrace;
   int* flags = static_cast<int*>(c->flags.p);
   hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
@@ -455,7 +508,9 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
                                 (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p, (uintptr_t)c->partials.p,
                                 (uintptr_t)c->step_partials.p, (uintptr_t)c->counters.p, (uintptr_t)count,
                                 (uintptr_t)c->pdl, (uintptr_t)c->seg_override,
-                                (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode};
+                                (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode, (uintptr_t)c->fused_cg,
+                                (uintptr_t)c->ws[W_R2].p, (uintptr_t)c->ws[W_S2].p, (uintptr_t)c->ws[W_W2].p,
+                                (uintptr_t)c->ws[W_W3].p, (uintptr_t)c->ws[W_GP].p};
   GraphEntry* ge = nullptr;
   for (GraphEntry& g : c->graphs)
     if (g.key == key) ge = &g;
@@ -492,18 +547,21 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
     *st = fail(HDG_ERR_CUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
     return true;
   }
-  c->launches += 2LL * count;
+  c->launches += (c->fused_cg ? 1LL : 2LL) * count;
   return true;
 }
 
 // The whole inner CG as one graph launch: a conditional WHILE node whose
-// body runs `kTrip` iterations and then the loop-control kernel.  Returns
-// false (graphs left to the chunked path) where the driver cannot build it.
-constexpr int kTrip = 4;
+// body runs `kTrip` iterations (kFusedPeriod with the fused step, whose
+// buffers rotate with that period) and then the loop-control kernel.
+// Returns false (graphs left to the chunked path) where the driver cannot
+// build it.
 template <typename T>
 bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, cudaStream_t s,
                    hdg_status* st) {
   *st = HDG_OK;
+  const int kTrip = c->fused_cg ? kFusedPeriod : 4;
+  const long long per_iter = c->fused_cg ? 1 : 2;
   if (!c->loop_graphs_enabled || c->prof_on) return false;
   if (ensure(c->loopctl, sizeof(unsigned int) * 4) != HDG_OK) return false;
   std::vector<uintptr_t> key = {0xC0DEu, sizeof(T), (uintptr_t)nrhs, (uintptr_t)dinv, (uintptr_t)lam_buf<T>(c).p,
@@ -513,7 +571,9 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
                                 (uintptr_t)c->partials.p, (uintptr_t)c->step_partials.p,
                                 (uintptr_t)c->counters.p, (uintptr_t)c->loopctl.p,
                                 (uintptr_t)c->seg_override, (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode,
-                                (uintptr_t)c->pdl};
+                                (uintptr_t)c->pdl, (uintptr_t)c->fused_cg, (uintptr_t)c->ws[W_R2].p,
+                                (uintptr_t)c->ws[W_S2].p, (uintptr_t)c->ws[W_W2].p, (uintptr_t)c->ws[W_W3].p,
+                                (uintptr_t)c->ws[W_GP].p};
   GraphEntry* ge = nullptr;
   for (GraphEntry& g : c->graphs)
     if (g.key == key) ge = &g;
@@ -582,7 +642,7 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
     *st = fail(HDG_ERR_CUDA, std::string("CG loop: ") + cudaGetErrorString(e));
     return true;
   }
-  c->launches += (long long)ntrip * (2LL * kTrip + 1);
+  c->launches += (long long)ntrip * (per_iter * kTrip + 1);
   return true;
 }
 
@@ -594,7 +654,15 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
                     std::vector<int>& iters, std::vector<int>& status, cudaStream_t s) {
   const long long T_ = c->ntrace;
   const long long tot = T_ * nrhs;
+  // the fused step (one tile-kernel launch per iteration) whenever the tile
+  // kernel is the operator; the two-kernel loop (operator, cg_step_kernel)
+  // for the other work splits
+  c->fused_cg = (c->fused_enabled && (c->op_variant == 0 || c->op_variant == 4)) ? 1 : 0;
   for (int i : {W_R, W_D, W_P, W_Q, W_U, W_S}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
+  if (c->fused_cg) {
+    for (int i : {W_R2, W_S2, W_W2, W_W3}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
+    HDG_TRY(ensure(c->ws[W_GP], sizeof(double) * (size_t)nrhs * std::max<long long>(c->red_blocks, c->nelem)));
+  }
   T* r = wsp<T>(c, W_R);
   T* d = wsp<T>(c, W_D);
   T* p = wsp<T>(c, W_P);
@@ -614,6 +682,8 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   if (sizeof(T) == 8) HDG_CUDA(cudaMemcpyAsync(r, rhat, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
   else { Timed t_(c, K_VEC, s); HDG_CUDA((hdg::launch_convert<double, float>(rhat, reinterpret_cast<float*>(r), tot, s))); }
   for (T* v : {d, p, q, u, wsp<T>(c, W_S)}) HDG_CUDA(cudaMemsetAsync(v, 0, sizeof(T) * tot, s));
+  if (c->fused_cg)
+    for (int i : {W_W2, W_W3}) HDG_CUDA(cudaMemsetAsync(c->ws[i].p, 0, sizeof(T) * tot, s));
   HDG_TRY(dot<T>(c, r, r, T_, nrhs, rz0, s, w));
   std::vector<int> hflags(nrhs);
   int maxit = 0;
@@ -627,14 +697,15 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   HDG_CUDA(cudaMemcpyAsync(tol_dev, tol_r.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
   // the per-rhs cap is the largest; per-rhs caps below it are enforced on the host afterwards
   { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_init(cg, flags, rz0, tol_dev, maxit, nrhs, s)); }
-  // u_0 = W r_0 (beta = 0 after init, u = 0)
-  { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, u, r, w, T_, nrhs, s)); }
-  const int chunk = 16;
+  // u_0 = W r_0 (beta = 0 after init, u = 0); the fused step forms u_0 itself
+  // (its first launch applies an update with alpha = beta = 0)
+  if (!c->fused_cg) { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_cg_pupdate<T>(cg, u, r, w, T_, nrhs, s)); }
+  const int chunk = c->fused_cg ? 3 * kFusedPeriod : 16;
   std::vector<hdg::CgScalars> hcg(nrhs);
   bool first = true;
   // first chunk eagerly (sets kernel attributes before any capture), then
   // the rest of the solve as one device-driven graph launch when possible
-  HDG_TRY(cg_iterations<T>(c, nrhs, dinv, w, r, d, p, q, chunk, s));
+  HDG_TRY(cg_iterations<T>(c, nrhs, dinv, w, r, d, p, q, c->fused_cg ? 2 * kFusedPeriod : chunk, s));
   first = false;
   {
     hdg_status gs = HDG_OK;
@@ -643,7 +714,7 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
       maxit = 0;   // done: skip the chunked loop below
     }
   }
-  for (int done_it = chunk; done_it < maxit; done_it += chunk) {
+  for (int done_it = c->fused_cg ? 2 * kFusedPeriod : chunk; done_it < maxit; done_it += chunk) {
     hdg_status gs = HDG_OK;
     // the first chunk runs eagerly (sets kernel attributes before any capture)
     if (first || !cg_graph<T>(c, nrhs, dinv, w, r, d, p, q, chunk, s, &gs))
@@ -898,18 +969,24 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
   HDG_TRY(ensure(c->ws[W_XHAT], esz * tot));
   HDG_TRY(ensure(c->ws[W_YHAT], esz * tot));
   HDG_CUDA(cudaMemsetAsync(c->ws[W_XHAT].p, 0x3c, esz * tot, s));   // finite, non-zero pattern
-  // candidate segment lengths (distinct splits of the x1-pencils) and slots
+  // candidate segment lengths (distinct splits of the x1-pencils) and slots;
+  // for the tile kernel: elements per tile, no slots
+  const bool tiles = c->op_variant == 0 || c->op_variant == 4;
   std::vector<int> segs = {0};
-  for (int sg = 1; sg <= c->mesh.ne[0]; ++sg) {
-    const int ns = (c->mesh.ne[0] + sg - 1) / sg;
-    if (sg > 1 && (c->mesh.ne[0] + sg - 2) / (sg - 1) == ns) continue;
-    if (sg <= 4 || sg == c->mesh.ne[0] || (sg & (sg - 1)) == 0) segs.push_back(sg);
+  if (tiles) {
+    for (int e : {2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32}) segs.push_back(e);
+  } else {
+    for (int sg = 1; sg <= c->mesh.ne[0]; ++sg) {
+      const int ns = (c->mesh.ne[0] + sg - 1) / sg;
+      if (sg > 1 && (c->mesh.ne[0] + sg - 2) / (sg - 1) == ns) continue;
+      if (sg <= 4 || sg == c->mesh.ne[0] || (sg & (sg - 1)) == 0) segs.push_back(sg);
+    }
   }
   std::vector<int> slots = {0};
   const int base = hdg::tpt_ppb(c->n);
   const int max_threads = prec == HDG_FP64 ? 320 : hdg::fast_max_threads(c->n);
   for (int pp : {base / 2, base - 1, base + 1, base * 3 / 2})
-    if (pp >= 1 && pp != base &&
+    if (!tiles && pp >= 1 && pp != base &&
         (prec == HDG_FP64 ? hdg::tpt_threads(c->n, pp) : hdg::fast_threads(c->n, pp)) <= max_threads)
       slots.push_back(pp);
   const int keep_seg = c->seg_override, keep_ppb = c->ppb_override;
@@ -967,10 +1044,16 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
 }
 
 hdg_status hdg_set_operator_variant(hdg_ctx* c, int variant, int elements_per_cta) {
-  if (!c || variant < 0 || variant > 3 || elements_per_cta < 0 || elements_per_cta * c->n > 128)
-    return fail(HDG_ERR_INVALID_ARG, "NULL context, variant outside 0..3 or x2-plane CTA above 128 threads");
+  if (!c || variant < 0 || variant > 4 || elements_per_cta < 0 || elements_per_cta * c->n > 128)
+    return fail(HDG_ERR_INVALID_ARG, "NULL context, variant outside 0..4 or x2-plane CTA above 128 threads");
   c->op_variant = variant;
   c->plane_epc = elements_per_cta;
+  return HDG_OK;
+}
+
+hdg_status hdg_set_cg_variant(hdg_ctx* c, int variant) {
+  if (!c || variant < 0 || variant > 1) return fail(HDG_ERR_INVALID_ARG, "NULL context or CG variant outside 0..1");
+  c->fused_enabled = variant == 0 ? 1 : 0;
   return HDG_OK;
 }
 

@@ -30,6 +30,10 @@ int tpt_blocks_per_sm(int mode, int n, int ppb);
 // CTAs hold kWarpSlotsPerCta one-warp slots
 constexpr int kWarpSlotsPerCta = 4;
 int warp_slots_blocks_per_sm(int n);
+// the apply with the tile kernel (tpt_tile.cuh), per storage precision
+cudaError_t launch_tile_f32(int n, const TptArgs<float, float>& a, int nrhs, cudaStream_t s);
+cudaError_t launch_tile_f64(int n, const TptArgs<double, double>& a, int nrhs, cudaStream_t s);
+cudaError_t launch_tile_bf16(int n, const TptArgs<float, __nv_bfloat16>& a, int nrhs, cudaStream_t s);
 // FP32 apply with the alternative work splits (hdg_set_operator_variant)
 cudaError_t launch_tpt_warp_slots(int n, const TptArgs<float, float>& a, int nrhs, cudaStream_t s);
 cudaError_t launch_tpt_planes(int n, const TptArgs<float, float>& a, int nrhs, cudaStream_t s);

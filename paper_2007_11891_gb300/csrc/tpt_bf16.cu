@@ -16,6 +16,7 @@ template <>
 cudaError_t launch_tpt<float, __nv_bfloat16>(int mode, int n, TptArgs<float, __nv_bfloat16> a, int nrhs,
                                              cudaStream_t s) {
   if (mode != TPT_APPLY) return cudaErrorInvalidValue;
+  if (a.variant == 3) return launch_tile_bf16(n, a, nrhs, s);
 #define FLB(N) fast_dispatch_dz<N, __nv_bfloat16>(a, nrhs, s)
   FAST_N_SWITCH(n, FLB)
 #undef FLB

@@ -22,6 +22,7 @@ int tpt_blocks_per_sm<float, float>(int mode, int n, int ppb) {
 
 template <>
 cudaError_t launch_tpt<float, float>(int mode, int n, TptArgs<float, float> a, int nrhs, cudaStream_t s) {
+  if (mode == TPT_APPLY && a.variant == 3) return launch_tile_f32(n, a, nrhs, s);
   if (mode == TPT_APPLY && a.variant == 2) return launch_tpt_warp_slots(n, a, nrhs, s);
   if (mode == TPT_APPLY && a.variant == 1) return launch_tpt_planes(n, a, nrhs, s);
   if (mode == TPT_APPLY) {

@@ -175,6 +175,28 @@ __device__ __forceinline__ void hook_finish(const CgHook& hook, int rhs, T dot, 
   }
 }
 
+// Vectors of the fused CG step of the tile kernel (tpt_tile.cuh): the launch
+// of iteration i + 1 applies the update of iteration i to each face value it
+// stages.  x and p are updated in place by the one owner of each face value;
+// r and s are read from one buffer and written to the other (a face value's
+// second reader, in another CTA, still reads the old values); w (= K u of
+// iteration i, complete) is read from one of three buffers, the operator
+// accumulates K u_{i+1} into the second, and the owners zero the third for
+// the launch after next.
+template <typename T>
+struct CgVecs {
+  T* x;
+  T* p;
+  const T* r_in;
+  T* r_out;
+  const T* s_in;
+  T* s_out;
+  const T* w_in;
+  T* w_zero;
+  const T* W;              // preconditioner weights, or null (W = I)
+  double* gpartials;       // [nrhs][gridDim.x] per-block partial sums of gamma = r . u
+};
+
 template <typename T, typename ST>
 struct TptArgs {
   MeshDev mesh;
@@ -202,7 +224,13 @@ struct TptArgs {
   const int* skip;              // per rhs: nonzero -> do nothing (converged), or null
   CgHook hook;                  // partials == null: no dot
   int pdl;                      // host: launch with programmatic stream serialization
-  int variant;                  // FP32 apply: 0 element runs (tpt_fast.cuh), 1 x2-planes (tpt_plane.cuh)
+  int variant;                  // apply kernel: 0 element runs (tpt_fast.cuh / tpt_kernel.cuh),
+                                // 1 x2-planes (tpt_plane.cuh), 2 warp slots (tpt_warp.cuh),
+                                // 3 element tiles (tpt_tile.cuh)
+  int sms;                      // host: SMs of the device (tile kernel grid)
+  int tile;                     // host: elements per tile of the tile kernel, 0 = automatic
+  int cg;                       // tile kernel: 1 = fused CG step (cgv), 0 = plain apply
+  CgVecs<T> cgv;
 };
 
 // Shared memory per pencil slot (elements of T): two buffers of the four

@@ -111,12 +111,20 @@ class HDG:
         _capi.check(_capi.lib().hdg_set_dz_mode(self._h, code), "hdg_set_dz_mode")
 
     def set_operator_variant(self, variant, elements_per_cta=0):
-        """FP32 operator tuning: 'auto', 'runs' (one thread per x1-line),
-        'planes' (one thread per x2-plane; elements_per_cta, 0 = automatic) or
-        'warps' (one warp per element slot)."""
-        code = {"auto": 0, "runs": 1, "planes": 2, "warps": 3}[variant]
+        """Operator kernel: 'auto' or 'tiles' (element tiles, every
+        precision), 'runs' (one thread per x1-line in element runs), and for
+        FP32 'planes' (one thread per x2-plane; elements_per_cta, 0 =
+        automatic) or 'warps' (one warp per element slot)."""
+        code = {"auto": 0, "runs": 1, "planes": 2, "warps": 3, "tiles": 4}[variant]
         _capi.check(_capi.lib().hdg_set_operator_variant(self._h, code, int(elements_per_cta)),
                     "hdg_set_operator_variant")
+
+    def set_cg_variant(self, variant):
+        """Inner CG iteration: 'fused' (one tile-kernel launch per iteration,
+        the default with the tile operator) or 'two_kernel' (operator, then
+        the vector update)."""
+        code = {"fused": 0, "two_kernel": 1}[variant]
+        _capi.check(_capi.lib().hdg_set_cg_variant(self._h, code), "hdg_set_cg_variant")
 
     def set_nodal_variant(self, variant):
         """FP64 nodal-basis apply: 'facewise' (transform every face once around
@@ -248,6 +256,16 @@ class HDG:
                                            ctypes.c_void_p(gl.data_ptr()), ctypes.byref(opts), info, _stream())
         _capi.check(st, "hdg_solve_adjoint")
         return gf.reshape(u.shape), gl, [info[i].as_dict() for i in range(nrhs)]
+
+
+def measure_fma_peak(precision="fp64"):
+    """Fused multiply-add rate of the current device in TFLOP/s (a register
+    FMA loop on every SM, CUDA events): the measured denominator of the
+    FP64 and FP32 pipe rooflines."""
+    out = ctypes.c_double()
+    st = _capi.lib().hdg_measure_fma_peak(_capi.PRECISION[precision], ctypes.byref(out), _stream())
+    _capi.check(st, "hdg_measure_fma_peak")
+    return out.value
 
 
 class HDGLowDim:

@@ -270,3 +270,30 @@ def test_polynomial_reproduction_high_degree(p, inner):
     assert info[0]["status"] == "OK"
     scale = np.abs(fld.u(X)).max()
     assert np.abs(u.cpu().numpy() - fld.u(X)).max() <= 1e-7 * scale
+
+
+@pytest.mark.parametrize("inner", ["fp32", "fp64"])
+@pytest.mark.parametrize("bc", [(0,) * 6, (1, 0, 1, 0, 1, 0), (0, 1, 1, 1, 0, 1)])
+def test_fused_and_two_kernel_cg_agree(inner, bc):
+    # one kernel per CG iteration (the operator launch applies the previous
+    # update to the face values it reads; each face value has one owner,
+    # also on Neumann sides) against the operator + update kernel pair: both
+    # reach the tolerance on the oracle's residual, with about the same
+    # iteration count (same iterates in exact arithmetic)
+    from paper_2007_11891_gb300 import HDG
+    ne, p, lam = (5, 4, 3), 4, 0.7
+    grid = _stretched(ne, 23)
+    pr = Problem(ne, grid, bc, p, 25.0, lam)
+    f = hdg_inputs.gaussian(pr.mesh.n_elem * (p + 1) ** 3, 24)
+    out = {}
+    for variant in ("fused", "two_kernel"):
+        h = HDG(ne, grid, bc, p, 25.0)
+        h.set_cg_variant(variant)
+        tr, u, info = h.solve(torch.tensor(f, device="cuda"), lam, tol=1e-10, inner=inner)
+        assert info[0]["status"] == "OK"
+        assert _oracle_residual(pr, tr.cpu().numpy(), f=f) <= 1e-10
+        out[variant] = (info[0]["iterations"], u)
+    it_f, it_t = out["fused"][0], out["two_kernel"][0]
+    assert abs(it_f - it_t) <= max(3, 0.05 * it_t), (it_f, it_t)
+    ref = out["two_kernel"][1].abs().max().item()
+    assert (out["fused"][1] - out["two_kernel"][1]).abs().max().item() <= 1e-8 * ref
