@@ -588,26 +588,44 @@ def run_sweep(args):
 
 def run_probe(args):
     """Short, untimed workload for ncu captures: set-up, one warm-up, then
-    `--steps` repetitions of the probed step (mixed solve, or one operator
-    application in FP32/FP64 in the transformed basis) on the bench workload.
+    `--steps` repetitions of the probed step on the chosen workload:
+      solve            mixed solve (fused CG step)
+      solve_two_kernel mixed solve with the operator + update kernel pair
+      apply32/64/bf16  one transformed-basis operator application
+      nodal_fused      one nodal FP64 apply by the one-kernel HDG-TP operator
+      lowdim2          one 2D operator application (512 x 512 elements, p = 8)
     With --eager the solve launches its kernels one by one (the same kernels
     as inside the CUDA graph)."""
     import torch
-    from paper_2007_11891_gb300 import HDG
+    from paper_2007_11891_gb300 import HDG, HDGLowDim
     torch.cuda.set_device(0)
     cfg = hdg_inputs.WORKLOADS[args.workload]
     ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"] or 1.0
-    h = HDG(ne, hdg_inputs.grid_lines(ne, cfg["stretched"]), (0,) * 6, p, hdg_inputs.TAU_HAT)
-    if args.eager:
-        h.profile(True)   # per-launch events; keeps the solver off CUDA graphs
-    if args.probe == "solve":
-        f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11890), device="cuda")
-        step = lambda: h.solve(f, lam, tol=1e-10, inner="fp32", return_u=True)
-    else:
-        dt = torch.float32 if args.probe == "apply32" else torch.float64
-        x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device="cuda", dtype=dt)
+    if args.probe == "lowdim2":
+        ne2 = (512, 512)
+        h = HDGLowDim(ne2, [np.linspace(0.0, 1.0, v + 1) for v in ne2], (0,) * 4, 8, hdg_inputs.TAU_HAT)
+        x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device="cuda")
         y = torch.empty_like(x)
-        step = lambda: h.apply(x, lam, basis="transformed", out=y)
+        step = lambda: h.apply(x, 1.0, basis="transformed", out=y)
+    else:
+        h = HDG(ne, hdg_inputs.grid_lines(ne, cfg["stretched"]), (0,) * 6, p, hdg_inputs.TAU_HAT)
+        if args.eager:
+            h.profile(True)   # per-launch events; keeps the solver off CUDA graphs
+        if args.probe in ("solve", "solve_two_kernel"):
+            if args.probe == "solve_two_kernel":
+                h.set_cg_variant("two_kernel")
+            f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11890), device="cuda")
+            step = lambda: h.solve(f, lam, tol=1e-10, inner="fp32", return_u=True)
+        elif args.probe == "nodal_fused":
+            h.set_nodal_variant("fused")
+            x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device="cuda")
+            y = torch.empty_like(x)
+            step = lambda: h.apply(x, lam, basis="nodal", out=y)
+        else:
+            dt = {"apply32": torch.float32, "apply64": torch.float64, "apply_bf16": torch.bfloat16}[args.probe]
+            x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device="cuda").to(dt)
+            y = torch.empty_like(x)
+            step = lambda: h.apply(x, lam, basis="transformed", out=y)
     step()
     torch.cuda.synchronize()
     for _ in range(args.steps):
@@ -625,7 +643,8 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="extra measurements instead of the bench line")
     ap.add_argument("--parts", default="operator,nodal,lowdim,paper,bf16,adjoint,batched",
                     help="sweep sections to run (comma-separated)")
-    ap.add_argument("--probe", choices=["solve", "apply32", "apply64"], help="untimed workload for ncu")
+    ap.add_argument("--probe", choices=["solve", "solve_two_kernel", "apply32", "apply64", "apply_bf16",
+                                        "nodal_fused", "lowdim2"], help="untimed workload for ncu")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(hdg_inputs.WORKLOADS))
     ap.add_argument("--eager", action="store_true",
                     help="probe: launch the CG loop kernel by kernel (no CUDA graphs), so that profilers that "

@@ -279,15 +279,22 @@ hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
 hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant, int elements_per_cta);
 
 /* Tuning (not part of the method): how an inner CG iteration runs.
- *   0 (default) one kernel per iteration when the operator kernel is the
- *     element-tile kernel (hdg_set_operator_variant 0 or 4): the launch of
- *     iteration i + 1 applies the CG update of iteration i to every face
- *     value it reads (each face value's one owner stores the new x, p, r, s)
- *     and applies the operator to the new search direction; the two inner
- *     products of the single-reduction CG are summed in the same launch;
+ *   0 (default) with the element-tile operator kernel
+ *     (hdg_set_operator_variant 0 or 4): the whole inner CG in one
+ *     cooperative launch of that kernel (every CTA resident; per iteration,
+ *     each CTA applies the CG update of the previous iteration to every face
+ *     value it reads -- each face value's one owner stores the new x, p, r,
+ *     s -- applies the operator to the new search direction, and after one
+ *     grid barrier every CTA forms the step scalars from all CTAs' partial
+ *     sums in the same order); where a cooperative launch is not possible,
+ *     as variant 2;
+ *   2 the same fused step, one launch per iteration (the last CTA of each
+ *     launch forms the step scalars), launched from a CUDA graph;
  *   1 two kernels per iteration: the operator, then the vector update.
- * Both compute the same CG iterates in exact arithmetic.
- * Errors: INVALID_ARG (NULL context, variant outside 0..1).               */
+ * All compute the same CG iterates in exact arithmetic.  A grid barrier that
+ * waits too long (CTAs not co-resident) ends the kernel and the solve
+ * returns HDG_ERR_CUDA.  Errors: INVALID_ARG (NULL context, variant outside
+ * 0..2).                                                                  */
 hdg_status hdg_set_cg_variant(hdg_ctx* ctx, int variant);
 
 /* Which kernel applies K in the nodal basis (hdg_apply with HDG_FP64 and

@@ -140,5 +140,35 @@ __device__ __forceinline__ void red_add(float* p, float v) {
 __device__ __forceinline__ void red_add(__nv_bfloat16* p, float v) {
   atomicAdd(p, __float2bfloat16_rn(v));
 }
+// Stores under a predicate (no branch around them); p is not dereferenced
+// when `on` is false.
+__device__ __forceinline__ void st_if(bool on, double* p, double v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.global.f64 [%1], %2;\n\t}"
+               ::"r"((int)on), "l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_if(bool on, float* p, float v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.global.f32 [%1], %2;\n\t}"
+               ::"r"((int)on), "l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_if(bool on, __nv_bfloat16* p, float v) {
+  const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q st.global.b16 [%1], %2;\n\t}"
+               ::"r"((int)on), "l"(p), "h"(b) : "memory");
+}
+// The same reductions under a predicate (no branch around them): the add is
+// issued only when `on`; p is not dereferenced otherwise.
+__device__ __forceinline__ void red_add_if(bool on, double* p, double v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.f64 [%1], %2;\n\t}"
+               ::"r"((int)on), "l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_if(bool on, float* p, float v) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.f32 [%1], %2;\n\t}"
+               ::"r"((int)on), "l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_if(bool on, __nv_bfloat16* p, float v) {
+  const unsigned short b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %0, 0;\n\t@q red.global.add.noftz.bf16 [%1], %2;\n\t}"
+               ::"r"((int)on), "l"(p), "h"(b) : "memory");
+}
 
 }  // namespace hdg

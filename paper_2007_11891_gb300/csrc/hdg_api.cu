@@ -111,6 +111,7 @@ struct hdg_ctx {
   int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
   int fused_cg = 0;       // the current inner CG runs the fused tile-kernel step
   int fused_enabled = 1;  // allow the fused step (hdg_set_cg_variant)
+  int persist_enabled = 1;  // run the fused step as one persistent cooperative launch
 };
 
 namespace {
@@ -119,8 +120,9 @@ enum Ws {
   W_XHAT = 0, W_YHAT, W_FHAT_T, W_RHAT, W_TMP, W_FVOL, W_GHAT, W_WVOL,
   W_R, W_D, W_P, W_Q, W_DOT, W_DOT2, W_U, W_S,
   // fused CG step (tile kernel): second r and s buffers, second and third w
-  // buffers, per-block gamma partials
-  W_R2, W_S2, W_W2, W_W3, W_GP
+  // buffers, per-block gamma partials; persistent CG: per-block delta
+  // partials and the grid-barrier words
+  W_R2, W_S2, W_W2, W_W3, W_GP, W_DP, W_BAR
 };
 
 hdg_status ensure(DevBuf& b, size_t bytes) {
@@ -467,6 +469,76 @@ hdg_status cg_fused_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* Wt,
   return HDG_OK;
 }
 
+// The whole inner CG of the fused step in one cooperative launch of the tile
+// kernel (CGM = 2): every CTA stays resident, one grid barrier per iteration.
+// Returns false (nothing launched) if the device cannot run it, so that the
+// caller runs the per-launch path.
+template <typename T>
+bool cg_persistent(hdg_ctx* c, int nrhs, const T* dinv, const T* Wt, cudaStream_t s, hdg_status* st) {
+  *st = HDG_OK;
+  if (!c->persist_enabled) return false;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return false;
+  }
+  const size_t pb = (size_t)std::max<long long>(c->red_blocks, c->nelem);
+  if (ensure(c->ws[W_DP], sizeof(double) * 2 * nrhs * pb) != HDG_OK ||
+      ensure(c->ws[W_GP], sizeof(double) * 2 * nrhs * pb) != HDG_OK ||
+      ensure(c->ws[W_BAR], sizeof(unsigned int) * (2 * (size_t)nrhs + 1)) != HDG_OK) {
+    g_last_error.clear();
+    return false;
+  }
+  unsigned int* bar = static_cast<unsigned int*>(c->ws[W_BAR].p);
+  int* err = reinterpret_cast<int*>(bar + 2 * nrhs);
+  if (cudaMemsetAsync(bar, 0, sizeof(unsigned int) * (2 * (size_t)nrhs + 1), s) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int* flags = static_cast<int*>(c->flags.p);
+  hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
+  double* uw = static_cast<double*>(c->scal.p) + nrhs;
+  hdg::TptArgs<T, T> a = base_args<T, T>(c, dinv, nrhs);
+  a.variant = 3;
+  a.cg = 2;
+  a.skip = flags;
+  a.hook = hdg::CgHook{wsp<double>(c, W_DP), static_cast<unsigned int*>(c->counters.p), uw, cg, flags, nullptr, 0};
+  a.pdl = 0;
+  a.x = nullptr;
+  a.cgv.x = wsp<T>(c, W_D);
+  a.cgv.p = wsp<T>(c, W_P);
+  a.cgv.W = Wt;
+  a.cgv.gpartials = wsp<double>(c, W_GP);
+  a.cgv.bar = bar;
+  a.cgv.err = err;
+  a.cgv.r_in = wsp<T>(c, W_R);
+  a.cgv.r_out = wsp<T>(c, W_R2);
+  a.cgv.s_in = wsp<T>(c, W_S);
+  a.cgv.s_out = wsp<T>(c, W_S2);
+  a.cgv.w_in = wsp<T>(c, W_Q);
+  a.y = wsp<T>(c, W_W2);
+  a.cgv.w_zero = wsp<T>(c, W_W3);
+  {
+    Timed t(c, sizeof(T) == 8 ? K_OP64 : K_OP32, s);
+    const cudaError_t e = hdg::launch_tpt<T, T>(hdg::TPT_APPLY, c->n, a, nrhs, s);
+    if (e != cudaSuccess) {
+      // e.g. a grid that cannot be co-resident: the per-launch path runs instead
+      cudaGetLastError();
+      c->persist_enabled = 0;
+      return false;
+    }
+  }
+  int herr = 0;
+  cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    *st = fail(HDG_ERR_CUDA, std::string("persistent CG: ") + cudaGetErrorString(e));
+    return true;
+  }
+  if (herr) *st = fail(HDG_ERR_CUDA, "persistent CG: a grid barrier timed out (CTAs not co-resident)");
+  return true;
+}
+
 template <typename T>
 hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, int count,
                          cudaStream_t s) {
@@ -703,11 +775,20 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   const int chunk = c->fused_cg ? 3 * kFusedPeriod : 16;
   std::vector<hdg::CgScalars> hcg(nrhs);
   bool first = true;
-  // first chunk eagerly (sets kernel attributes before any capture), then
+  // the fused step as one persistent launch when the device allows it; else
+  // the first chunk eagerly (sets kernel attributes before any capture), then
   // the rest of the solve as one device-driven graph launch when possible
-  HDG_TRY(cg_iterations<T>(c, nrhs, dinv, w, r, d, p, q, c->fused_cg ? 2 * kFusedPeriod : chunk, s));
-  first = false;
-  {
+  bool persisted = false;
+  if (c->fused_cg) {
+    hdg_status ps = HDG_OK;
+    persisted = cg_persistent<T>(c, nrhs, dinv, w, s, &ps);
+    HDG_TRY(ps);
+  }
+  if (persisted) {
+    maxit = 0;
+  } else {
+    HDG_TRY(cg_iterations<T>(c, nrhs, dinv, w, r, d, p, q, c->fused_cg ? 2 * kFusedPeriod : chunk, s));
+    first = false;
     hdg_status gs = HDG_OK;
     if (cg_loop_graph<T>(c, nrhs, dinv, w, r, d, p, q, s, &gs)) {
       HDG_TRY(gs);
@@ -1052,8 +1133,9 @@ hdg_status hdg_set_operator_variant(hdg_ctx* c, int variant, int elements_per_ct
 }
 
 hdg_status hdg_set_cg_variant(hdg_ctx* c, int variant) {
-  if (!c || variant < 0 || variant > 1) return fail(HDG_ERR_INVALID_ARG, "NULL context or CG variant outside 0..1");
-  c->fused_enabled = variant == 0 ? 1 : 0;
+  if (!c || variant < 0 || variant > 2) return fail(HDG_ERR_INVALID_ARG, "NULL context or CG variant outside 0..2");
+  c->fused_enabled = variant != 1 ? 1 : 0;
+  c->persist_enabled = variant == 0 ? 1 : 0;
   return HDG_OK;
 }
 

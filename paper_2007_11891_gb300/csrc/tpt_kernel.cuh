@@ -194,7 +194,10 @@ struct CgVecs {
   const T* w_in;
   T* w_zero;
   const T* W;              // preconditioner weights, or null (W = I)
-  double* gpartials;       // [nrhs][gridDim.x] per-block partial sums of gamma = r . u
+  double* gpartials;       // per-block partial sums of gamma = r . u: [nrhs][gridDim.x]
+                           // (persistent kernel: [2][nrhs][gridDim.x])
+  unsigned int* bar;       // persistent kernel: [nrhs][2] grid-barrier words, zero at launch
+  int* err;                // persistent kernel: set when a grid barrier gave up
 };
 
 template <typename T, typename ST>

@@ -59,17 +59,40 @@ constexpr int kTileMaxThreads = 384;
 // elements per thread and phase (E = G x rounds): the six face values of each
 // are loaded into registers before any is stored, 24 FP32 or 12 FP64
 // registers' worth at most, which keeps the FP64 instantiations free of spills
-template <typename T, bool CG = false>
-__host__ __device__ constexpr int tile_rounds() { return CG ? (sizeof(T) == 8 ? 1 : 2) : (sizeof(T) == 8 ? 2 : 4); }
+template <typename T, int CGM = 0>
+__host__ __device__ constexpr int tile_rounds() { return CGM ? 1 : (sizeof(T) == 8 ? 2 : 4); }
 // face offsets of a tile element: x1 lo/hi, x2 lo/hi, x3 lo/hi (face base,
 // -1 on a Dirichlet plane), element index, flags
-struct TileOff {
+struct __align__(16) TileOff {
   int f[6];
   int elem;
   int flags;   // 1: next element of the tile in the same x1-pencil; 2: previous
                // one; 4: low x1-plane is the domain boundary; 8: high one;
                // 16, 32: low x2-, x3-plane is the domain boundary
 };
+
+__device__ __forceinline__ void load_met(const float* p, float& d0, float& d1, float& d2, float& d3) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  d0 = v.x; d1 = v.y; d2 = v.z; d3 = v.w;
+}
+__device__ __forceinline__ void load_met(const double* p, double& d0, double& d1, double& d2, double& d3) {
+  const double2 v = reinterpret_cast<const double2*>(p)[0], w = reinterpret_cast<const double2*>(p)[1];
+  d0 = v.x; d1 = v.y; d2 = w.x; d3 = w.y;
+}
+
+template <int CGM, typename T>
+__device__ __forceinline__ T ld_state(const T* p) {
+  if constexpr (CGM == 2) return __ldcg(p);
+  else return *p;
+}
+
+__device__ __forceinline__ TileOff load_off(const TileOff* p) {
+  const int4 a = reinterpret_cast<const int4*>(p)[0], b = reinterpret_cast<const int4*>(p)[1];
+  TileOff o;
+  o.f[0] = a.x; o.f[1] = a.y; o.f[2] = a.z; o.f[3] = a.w;
+  o.f[4] = b.x; o.f[5] = b.y; o.elem = b.z; o.flags = b.w;
+  return o;
+}
 
 // End of a fused CG launch (launch i + 1): delta = u^T K u from the element
 // contributions and gamma = r . u from the face owners, both of iteration
@@ -120,6 +143,90 @@ __device__ __forceinline__ void hook_finish_cg(const CgHook& hook, double* gpart
   }
 }
 
+// Generation barrier over the gridDim.x CTAs of one right-hand side row of a
+// cooperative launch (every CTA resident), called by one thread per CTA after
+// the CTA's memory operations were fenced.  bar[0] counts arrivals, bar[1]
+// holds the number of barriers passed; the last CTA to arrive resets the
+// count and advances the generation.  Every wait is bounded: after
+// kBarrierSpins polls the barrier gives up, sets *err and returns 0, so a
+// fault in the launch configuration ends the kernel instead of hanging it.
+constexpr long long kBarrierSpins = 1LL << 20;
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int grid_barrier(unsigned int* bar, unsigned int gen, int* err) {
+  const unsigned int arrived = atomicAdd(bar, 1u);
+  if (arrived == gridDim.x - 1) {
+    atomicExch(bar, 0u);
+    __threadfence();
+    atomicExch(bar + 1, gen + 1u);
+    return 1;
+  }
+  for (long long spin = 0; spin < kBarrierSpins; ++spin) {
+    if (ld_acquire(bar + 1) != gen) {
+      __threadfence();
+      return 1;
+    }
+    __nanosleep(64);
+  }
+  atomicExch(err, 1);
+  return 0;
+}
+
+// End of one iteration of the persistent CG kernel (every CTA): per-block
+// partial sums of delta = u^T K u and gamma = r . u, one grid barrier, then
+// the step scalars of the next iteration formed by every CTA from all
+// partials in the same fixed order (deterministic, identical in every CTA).
+// The partials are double-buffered by the parity of the iteration.  Returns
+// false if the barrier gave up.
+template <typename T>
+__device__ __forceinline__ bool persistent_step(const CgHook& hook, const CgVecs<T>& v, int rhs, int iter, T dot,
+                                                T gam, CgScalars* s_cg, unsigned int* bar_gen) {
+  __shared__ double psum[2][32];
+  __shared__ int ok;
+  const int tid = threadIdx.x;
+  const int nb = gridDim.x;
+  const T dv = warp_sum(dot), gv = warp_sum(gam);
+  if ((tid & 31) == 0) {
+    psum[0][tid >> 5] = static_cast<double>(dv);
+    psum[1][tid >> 5] = static_cast<double>(gv);
+  }
+  __threadfence();   // this thread's stores and reductions of the iteration
+  __syncthreads();
+  const long long base = ((long long)(iter & 1) * gridDim.y + rhs) * nb;
+  if (tid == 0) {
+    double sd = 0.0, sg = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) {
+      sd += psum[0][w];
+      sg += psum[1][w];
+    }
+    hook.partials[base + blockIdx.x] = 0.5 * sd;
+    v.gpartials[base + blockIdx.x] = sg;
+    __threadfence();
+    ok = grid_barrier(v.bar + 2 * rhs, *bar_gen, v.err);
+    *bar_gen += 1u;
+  }
+  __syncthreads();
+  if (!ok) return false;
+  if (tid < 32) {
+    double sd = 0.0, sg = 0.0;
+    for (int b = tid; b < nb; b += 32) {
+      sd += __ldcg(hook.partials + base + b);
+      sg += __ldcg(v.gpartials + base + b);
+    }
+    sd = warp_sum(sd);
+    sg = warp_sum(sg);
+    if (tid == 0) {
+      int flag = 0;
+      cg_scalars(s_cg, *s_cg, &flag, sd, sg);
+    }
+  }
+  __syncthreads();
+  return true;
+}
+
 // Sum of the two contributions to a face value formed inside a tile, as the
 // two additions onto zero would form it: FP32/FP64 storage a + b; BF16
 // storage rounds each contribution to BF16 first (as red_add does) and the
@@ -133,8 +240,23 @@ __device__ __forceinline__ T pair_sum(T a, T b) {
     return a + b;
 }
 
-template <typename T, typename ST, int N, int DZM, bool CG = false>
-__global__ void __launch_bounds__(kTileMaxThreads, sizeof(T) == 4 ? 3 : 2) tpt_tile_kernel(const TptArgs<T, ST> a) {
+// Element groups G of a CTA (n^2 G threads, at most kTileMaxThreads, G <=
+// kTileMaxE) for degree n, and the CTA size it gives.
+__host__ __device__ constexpr int tile_groups(int n) {
+  return kTileMaxThreads / (n * n) < 1 ? 1 : (kTileMaxThreads / (n * n) > kTileMaxE ? kTileMaxE : kTileMaxThreads / (n * n));
+}
+// CTA size: n^2 G working threads, rounded up to whole warps (the padding
+// threads take part in barriers and warp reductions only)
+__host__ __device__ constexpr int tile_cta_threads(int n) { return (n * n * tile_groups(n) + 31) / 32 * 32; }
+
+// The exact CTA size in the launch bounds lets the compiler give each thread
+// the registers of three (FP32) or two (FP64) resident CTAs.
+// CGM: 0 operator application; 1 fused CG step (one iteration per launch);
+// 2 persistent CG (every iteration of an inner solve in one cooperative
+// launch, one grid barrier per iteration).
+template <typename T, typename ST, int N, int DZM, int CGM = 0>
+__global__ void __launch_bounds__(tile_cta_threads(N), sizeof(T) == 4 ? (CGM ? 2 : 3) : (CGM ? 1 : 2)) tpt_tile_kernel(const TptArgs<T, ST> a) {
+  constexpr bool CG = CGM > 0;
   constexpr bool DZC = DZM == 1;
   constexpr int N2 = N * N, NE = (N + 1) / 2;
   constexpr int R = tile_row<T, N>();
@@ -154,7 +276,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, sizeof(T) == 4 ? 3 : 2) tpt_t
   T* OXL = X1H + E * N2;
   T* OXH = OXL + E * N2;
   __shared__ TileOff s_off[2][kTileMaxE];
-  __shared__ T s_met[2][kTileMaxE][4];
+  __shared__ __align__(16) T s_met[2][kTileMaxE][4];
   __shared__ CgScalars s_cg;
 
   const int rhs = blockIdx.y;
@@ -212,7 +334,8 @@ __global__ void __launch_bounds__(kTileMaxThreads, sizeof(T) == 4 ? 3 : 2) tpt_t
   // the x1-line (j, k) = (qa, qb) in pass 1 and the face node (i, m) = (qa, qb)
   // of the x2/x3 contractions in pass 2, for the elements g, g + G, ... of
   // every tile; all of its index arithmetic is done once here
-  const int q = tid % N2, g = tid / N2;
+  const bool active = tid < N2 * G;
+  const int q = tid % N2, g = active ? tid / N2 : 0;
   const int qa = q % N, qb = q / N;
   const T cj = a.tab.c[qa], ck = a.tab.c[qb];
   const T lj = a.tab.lam[qa], lk = a.tab.lam[qb];
@@ -227,49 +350,48 @@ __global__ void __launch_bounds__(kTileMaxThreads, sizeof(T) == 4 ? 3 : 2) tpt_t
     static_for<0, N>([&](auto ic) { dzr[decltype(ic)::value] = dz[decltype(ic)::value]; });
   }
 
-  int tile = blockIdx.x;
-  int buf = 0;
-  tile_offsets(tile, buf);
-  __syncthreads();
-
+  __syncthreads();   // s_cg (hook_prefetch) visible to every thread
   // fused CG step: the step scalars of iteration i (from the previous
-  // launch's last block, read by hook_prefetch before the barrier above)
+  // launch's last block, or in the persistent kernel from this CTA's own
+  // reduction after the previous grid barrier)
   T al = T(0), be = T(0), gam = T(0);
+  unsigned int bar_gen = 0;   // persistent kernel: grid barriers passed
   if constexpr (CG) {
     al = static_cast<T>(s_cg.alpha);
     be = static_cast<T>(s_cg.beta);
   }
-  // the value of a face node the operator acts on: the stored input, or in
+  // The value of a face node the operator acts on: the stored input, or in
   // CG mode u_{i+1} = W r_{i+1} from the update of iteration i; the face's
   // owner (the element below it, or its only element) also stores the
   // updated x, p, r, s, zeroes the w buffer of the launch after next and
-  // adds its r . u to gamma
-  auto face_value = [&](int off_, bool owner) -> T {
-    if constexpr (!CG) {
-      (void)owner;
-      return load_as<ST, T>(xin + off_);
-    } else {
-      const CgVecs<T>& v = a.cgv;
-      const long long o_ = toff + off_;
-      const T r = v.r_in[o_], w = v.w_in[o_], sv = v.s_in[o_];
-      const T wt = v.W ? v.W[o_] : T(1);
-      const T sn = fma(be, sv, w);
-      const T rn = fma(-al, sn, r);
-      const T un = wt * rn;
-      if (owner) {
-        const T pn = fma(be, v.p[o_], wt * r);
-        v.x[o_] = fma(al, pn, v.x[o_]);
-        v.p[o_] = pn;
-        v.s_out[o_] = sn;
-        v.r_out[o_] = rn;
-        v.w_zero[o_] = T(0);
-        gam = fma(un, rn, gam);
-      }
-      return un;
-    }
-  };
+  // adds its r . u to gamma.  In CG mode every load of the thread's six face
+  // values is issued before any of them is used or stored (the vectors are
+  // distinct buffers, declared so through restrict-qualified copies).
+  T* __restrict__ vx = a.cgv.x;
+  T* __restrict__ vp = a.cgv.p;
+  const T* __restrict__ vW = a.cgv.W;
+  constexpr int kR = tile_rounds<T, CGM>();
 
-  constexpr int kR = tile_rounds<T, CG>();
+  // the persistent kernel's iterations; one pass for the other modes
+  for (int iter = 0;; ++iter) {
+  // buffers of this iteration: r and s rotate with period 2, w with period 3
+  // (the persistent kernel rotates them itself, launch by launch otherwise)
+  const int i2 = CGM == 2 ? iter % 2 : 0, i3 = CGM == 2 ? iter % 3 : 0;
+  const T* r_b[2] = {a.cgv.r_in, a.cgv.r_out};
+  const T* s_b[2] = {a.cgv.s_in, a.cgv.s_out};
+  const T* w_b[3] = {a.cgv.w_in, reinterpret_cast<const T*>(a.y), a.cgv.w_zero};
+  const T* __restrict__ vr = r_b[i2];
+  T* __restrict__ vro = const_cast<T*>(r_b[i2 ^ 1]);
+  const T* __restrict__ vs = s_b[i2];
+  T* __restrict__ vso = const_cast<T*>(s_b[i2 ^ 1]);
+  const T* __restrict__ vw = w_b[i3];
+  T* __restrict__ vwz = const_cast<T*>(w_b[(i3 + 2) % 3]);
+  if constexpr (CGM == 2) yout = reinterpret_cast<ST*>(const_cast<T*>(w_b[(i3 + 1) % 3])) + toff;
+
+  int tile = blockIdx.x;
+  int buf = 0;
+  tile_offsets(tile, buf);
+  __syncthreads();
   for (; tile < ntiles; tile += gridDim.x, buf ^= 1) {
     const TileOff* off = s_off[buf];
     // ---- 1. staging: every load of the thread's elements first ---------------
@@ -278,19 +400,58 @@ __global__ void __launch_bounds__(kTileMaxThreads, sizeof(T) == 4 ? 3 : 2) tpt_t
       constexpr int r = decltype(rc)::value;
       T* w = v[r];
       w[0] = w[1] = w[2] = w[3] = w[4] = w[5] = T(0);
-      if (r < RR) {
-        const TileOff& o = off[g + r * G];
-        if (o.f[2] >= 0) w[0] = face_value(o.f[2] + q, (o.flags & 16) != 0);
-        if (o.f[3] >= 0) w[1] = face_value(o.f[3] + q, true);
-        if (o.f[4] >= 0) w[2] = face_value(o.f[4] + q, (o.flags & 32) != 0);
-        if (o.f[5] >= 0) w[3] = face_value(o.f[5] + q, true);
-        if (o.f[0] >= 0) w[4] = face_value(o.f[0] + q, (o.flags & 6) != 0);
-        if (!(o.flags & 1) && o.f[1] >= 0) w[5] = face_value(o.f[1] + q, true);
+      if (active && r < RR) {
+        const TileOff o = load_off(off + g + r * G);
+        if constexpr (!CG) {
+          if (o.f[2] >= 0) w[0] = load_as<ST, T>(xin + o.f[2] + q);
+          if (o.f[3] >= 0) w[1] = load_as<ST, T>(xin + o.f[3] + q);
+          if (o.f[4] >= 0) w[2] = load_as<ST, T>(xin + o.f[4] + q);
+          if (o.f[5] >= 0) w[3] = load_as<ST, T>(xin + o.f[5] + q);
+          if (o.f[0] >= 0) w[4] = load_as<ST, T>(xin + o.f[0] + q);
+          if (!(o.flags & 1) && o.f[1] >= 0) w[5] = load_as<ST, T>(xin + o.f[1] + q);
+        } else {
+          // slots x2 lo/hi, x3 lo/hi, x1 lo, x1 hi: offset (or -1), owner
+          const int fo[6] = {o.f[2], o.f[3], o.f[4], o.f[5], o.f[0], (o.flags & 1) ? -1 : o.f[1]};
+          const bool own[6] = {(o.flags & 16) != 0, true, (o.flags & 32) != 0, true, (o.flags & 6) != 0, true};
+          T lr[6], lw[6], ls[6], lW[6], lp[6], lx[6];
+          static_for<0, 6>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            const long long oo = toff + (fo[k] >= 0 ? fo[k] + q : 0);
+            const bool on = fo[k] >= 0, ow = on && own[k];
+            // the persistent kernel reads vectors other CTAs wrote during
+            // this launch: through L2 (ld.cg), never a stale L1 line
+            lr[k] = on ? ld_state<CGM>(vr + oo) : T(0);
+            lw[k] = on ? ld_state<CGM>(vw + oo) : T(0);
+            ls[k] = on ? ld_state<CGM>(vs + oo) : T(0);
+            lW[k] = (on && vW) ? vW[oo] : T(1);
+            lp[k] = ow ? ld_state<CGM>(vp + oo) : T(0);
+            lx[k] = ow ? ld_state<CGM>(vx + oo) : T(0);
+          });
+          static_for<0, 6>([&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            if (fo[k] >= 0) {
+              const long long oo = toff + fo[k] + q;
+              const T sn = fma(be, ls[k], lw[k]);
+              const T rn = fma(-al, sn, lr[k]);
+              const T un = lW[k] * rn;
+              w[k] = un;
+              if (own[k]) {
+                const T pn = fma(be, lp[k], lW[k] * lr[k]);
+                vx[oo] = fma(al, pn, lx[k]);
+                vp[oo] = pn;
+                vso[oo] = sn;
+                vro[oo] = rn;
+                vwz[oo] = T(0);
+                gam = fma(un, rn, gam);
+              }
+            }
+          });
+        }
       }
     });
     static_for<0, kR>([&](auto rc) {
       constexpr int r = decltype(rc)::value;
-      if (r < RR) {
+      if (active && r < RR) {
         const int el = g + r * G;
         const T* w = v[r];
         // x2 face node (i, k) -> row k; x3 face node (i, j) -> row j
@@ -309,11 +470,12 @@ __global__ void __launch_bounds__(kTileMaxThreads, sizeof(T) == 4 ? 3 : 2) tpt_t
     __syncthreads();
 
     // ---- 2. pass 1: the x1-line (j, k) of each element --------------------------
-    for (int r = 0; r < RR; ++r) {
+    for (int r = 0; r < (active ? RR : 0); ++r) {
       const int el = g + r * G;
-      const TileOff& o = off[el];
+      const TileOff o = load_off(off + el);
       if (o.elem < 0) continue;
-      const T d0 = s_met[buf][el][0], d1 = s_met[buf][el][1], d2 = s_met[buf][el][2], d3 = s_met[buf][el][3];
+      T d0, d1, d2, d3;
+      load_met(&s_met[buf][el][0], d0, d1, d2, d3);
       const int it = el * N2 + q;
       const T xl = X1[it];
       const T xh = (o.flags & 1) ? X1[it + N2] : X1H[it];
@@ -328,6 +490,55 @@ __global__ void __launch_bounds__(kTileMaxThreads, sizeof(T) == 4 ? 3 : 2) tpt_t
       if constexpr (DZC) dzb = fma(d3, lk, fma(d2, lj, lam_r * d0));
       T* Ur = U + el * N2 * R + line;
       T Pp = T(0), Pm = T(0);
+      if constexpr (std::is_same<T, float>::value) {
+        // FP32: pairs of points (i, i + 1) in packed two-lane FP32 arithmetic
+        // (one FFMA2/FMUL2 per pair); the x1 contraction keeps one two-lane
+        // accumulator per parity combination of a pair
+        float2 pEE = make_float2(0.f, 0.f), pOO = pEE, pEO = pEE;
+        const float2 cjd2v = make_float2(cjd2, cjd2), ckd3v = make_float2(ckd3, ckd3);
+        static_for<0, NQ>([&](auto qc) {
+          constexpr int qq = decltype(qc)::value;
+          const float4 bv = *reinterpret_cast<const float4*>(Bs + 4 * qq);
+          const float4 cv = *reinterpret_cast<const float4*>(Cs + 4 * qq);
+          float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
+          if constexpr (DZM == 2) dv = *reinterpret_cast<const float4*>(dzg + 4 * qq);
+          (void)dv;
+          float2 uh[2];
+          static_for<0, 2>([&](auto hc) {
+            constexpr int hh = decltype(hc)::value;
+            constexpr int i0 = 4 * qq + 2 * hh, i1 = i0 + 1;
+            if constexpr (i0 < N) {
+              constexpr bool e0 = i0 < NE, e1 = i1 < NE, v1 = i1 < N;
+              const float c0 = a.tab.c[i0], c1 = v1 ? a.tab.c[i1] : 0.f;
+              float2 F = __fmul2_rn(make_float2(c0, c1), make_float2(e0 ? Ap : Am, e1 ? Ap : Am));
+              F = __ffma2_rn(cjd2v, hh == 0 ? make_float2(bv.x, bv.y) : make_float2(bv.z, bv.w), F);
+              F = __ffma2_rn(ckd3v, hh == 0 ? make_float2(cv.x, cv.y) : make_float2(cv.z, cv.w), F);
+              float2 inv;
+              if constexpr (DZM == 0) {
+                inv = make_float2(dzr[i0], v1 ? dzr[i1] : 0.f);
+              } else if constexpr (DZC) {
+                const float2 den = __ffma2_rn(make_float2(d1, d1),
+                                              make_float2(a.tab.lam[i0], v1 ? a.tab.lam[i1] : 0.f),
+                                              make_float2(dzb, dzb));
+                inv = make_float2(dz_recip(den.x), v1 ? dz_recip(den.y) : 0.f);
+              } else {
+                inv = hh == 0 ? make_float2(dv.x, dv.y) : make_float2(dv.z, dv.w);
+              }
+              const float2 u = __fmul2_rn(F, inv);
+              uh[hh] = u;
+              const float2 cc = make_float2(c0, c1);
+              if constexpr (e0 && e1) pEE = __ffma2_rn(cc, u, pEE);
+              else if constexpr (!e0 && !e1) pOO = __ffma2_rn(cc, u, pOO);
+              else pEO = __ffma2_rn(cc, u, pEO);
+            } else {
+              uh[hh] = make_float2(0.f, 0.f);
+            }
+          });
+          *reinterpret_cast<float4*>(Ur + 4 * qq) = make_float4(uh[0].x, uh[0].y, uh[1].x, uh[1].y);
+        });
+        Pp = (pEE.x + pEE.y) + pEO.x;
+        Pm = (pOO.x + pOO.y) + pEO.y;
+      } else {
       static_for<0, NQ>([&](auto qc) {
         constexpr int qq = decltype(qc)::value;
         const V bv = *reinterpret_cast<const V*>(Bs + VL * qq);
@@ -357,6 +568,7 @@ __global__ void __launch_bounds__(kTileMaxThreads, sizeof(T) == 4 ? 3 : 2) tpt_t
         });
         *reinterpret_cast<V*>(Ur + VL * qq) = uv;
       });
+      }
       // x1 face residuals of this line (node (j, k) of the lo and hi faces)
       const T sum = d1 * (hs * S1 - T(2) * Pp), dif = d1 * (hd * D1 - T(2) * Pm);
       OXL[it] = T(0.5) * (sum + dif);
@@ -366,53 +578,94 @@ __global__ void __launch_bounds__(kTileMaxThreads, sizeof(T) == 4 ? 3 : 2) tpt_t
     __syncthreads();
 
     // ---- 3. pass 2: x2/x3 contractions at the node (i, m), x1 faces -------------
-    for (int r = 0; r < RR; ++r) {
+    for (int r = 0; r < (active ? RR : 0); ++r) {
       const int el = g + r * G;
-      const TileOff& o = off[el];
+      const TileOff o = load_off(off + el);
       if (o.elem < 0) continue;
       const T d2 = s_met[buf][el][2], d3 = s_met[buf][el][3];
       const T* Uq = U + el * N2 * R + R * N * qb + qa;   // (i, j = mo, k = m): + R mo
       const T* Uk = U + el * N2 * R + R * qb + qa;       // (i, j = m, k = mo): + R N mo
       T Qp = T(0), Qm = T(0), Rp = T(0), Rm = T(0);
-      static_for<0, N>([&](auto mc) {
-        constexpr int mo = decltype(mc)::value;
-        const T uq = Uq[R * mo];
-        const T ur = Uk[R * N * mo];
-        if constexpr (mo < NE) { Qp = fma(a.tab.c[mo], uq, Qp); Rp = fma(a.tab.c[mo], ur, Rp); }
-        else                   { Qm = fma(a.tab.c[mo], uq, Qm); Rm = fma(a.tab.c[mo], ur, Rm); }
-      });
+      if constexpr (std::is_same<T, float>::value) {
+        // FP32: the x2 and x3 contractions as one two-lane accumulator per parity
+        float2 QRp = make_float2(0.f, 0.f), QRm = QRp;
+        static_for<0, N>([&](auto mc) {
+          constexpr int mo = decltype(mc)::value;
+          const float2 uu = make_float2(Uq[R * mo], Uk[R * N * mo]);
+          const float2 cm = make_float2(a.tab.c[mo], a.tab.c[mo]);
+          if constexpr (mo < NE) QRp = __ffma2_rn(cm, uu, QRp);
+          else QRm = __ffma2_rn(cm, uu, QRm);
+        });
+        Qp = QRp.x; Rp = QRp.y; Qm = QRm.x; Rm = QRm.y;
+      } else {
+        static_for<0, N>([&](auto mc) {
+          constexpr int mo = decltype(mc)::value;
+          const T uq = Uq[R * mo];
+          const T ur = Uk[R * N * mo];
+          if constexpr (mo < NE) { Qp = fma(a.tab.c[mo], uq, Qp); Rp = fma(a.tab.c[mo], ur, Rp); }
+          else                   { Qm = fma(a.tab.c[mo], uq, Qm); Rm = fma(a.tab.c[mo], ur, Rm); }
+        });
+      }
       {  // x2 faces, node (i, k = m)
         const T* s2 = SD2 + el * 2 * N * R + node;
         const T Sv = s2[0], Dv = s2[N * R];
         const T sum = d2 * (hs * Sv - T(2) * Qp), dif = d2 * (hd * Dv - T(2) * Qm);
-        if (o.f[2] >= 0) red_add(yout + o.f[2] + q, T(0.5) * (sum + dif));
-        if (o.f[3] >= 0) red_add(yout + o.f[3] + q, T(0.5) * (sum - dif));
+        red_add_if(o.f[2] >= 0, yout + (max(o.f[2], 0) + q), T(0.5) * (sum + dif));
+        red_add_if(o.f[3] >= 0, yout + (max(o.f[3], 0) + q), T(0.5) * (sum - dif));
         dot = fma(Sv, sum, fma(Dv, dif, dot));
       }
       {  // x3 faces, node (i, j = m)
         const T* s3 = SD3 + el * 2 * N * R + node;
         const T Sv = s3[0], Dv = s3[N * R];
         const T sum = d3 * (hs * Sv - T(2) * Rp), dif = d3 * (hd * Dv - T(2) * Rm);
-        if (o.f[4] >= 0) red_add(yout + o.f[4] + q, T(0.5) * (sum + dif));
-        if (o.f[5] >= 0) red_add(yout + o.f[5] + q, T(0.5) * (sum - dif));
+        red_add_if(o.f[4] >= 0, yout + (max(o.f[4], 0) + q), T(0.5) * (sum + dif));
+        red_add_if(o.f[5] >= 0, yout + (max(o.f[5], 0) + q), T(0.5) * (sum - dif));
         dot = fma(Sv, sum, fma(Dv, dif, dot));
       }
-      // x1 faces, node q: the lo face of this element, and its hi face where
-      // the next element of the tile does not own it
+      // x1 faces, node q: the lo face of this element (stored when the tile
+      // holds both of its contributions or it is a boundary face, else added),
+      // and its hi face where the next element of the tile does not own it
       const int it = el * N2 + q;
-      if (o.f[0] >= 0) {
-        if (o.flags & 2) store_from<ST, T>(yout + o.f[0] + q, pair_sum<ST>(OXL[it], OXH[it - N2]));
-        else if (o.flags & 4) store_from<ST, T>(yout + o.f[0] + q, OXL[it]);
-        else red_add(yout + o.f[0] + q, OXL[it]);
+      {
+        const bool on = o.f[0] >= 0, st = on && (o.flags & 6) != 0;
+        // (it - N2 stays inside the shared buffers for el = 0: OXH follows OXL)
+        const T lv = (o.flags & 2) ? pair_sum<ST>(OXL[it], OXH[it - N2]) : OXL[it];
+        ST* dst = yout + (max(o.f[0], 0) + q);
+        st_if(st, dst, lv);
+        red_add_if(on && !st, dst, lv);
       }
-      if (o.f[1] >= 0 && !(o.flags & 1)) {
-        if (o.flags & 8) store_from<ST, T>(yout + o.f[1] + q, OXH[it]);
-        else red_add(yout + o.f[1] + q, OXH[it]);
+      {
+        const bool on = o.f[1] >= 0 && !(o.flags & 1), st = on && (o.flags & 8) != 0;
+        ST* dst = yout + (max(o.f[1], 0) + q);
+        st_if(st, dst, OXH[it]);
+        red_add_if(on && !st, dst, OXH[it]);
       }
     }
     __syncthreads();   // the next tile restages every buffer
   }
+  if constexpr (CGM != 2) break;
+  else {
+    // end of iteration `iter`: per-block partial sums of delta and gamma
+    // (buffer by the parity of the iteration: a fast CTA may write the next
+    // iteration's partials while a slow one still reads these), one grid
+    // barrier, then every CTA forms the step scalars from all partials in the
+    // same fixed order, so that every CTA takes the same decisions
+    if (!persistent_step(a.hook, a.cgv, rhs, iter, dot, gam, &s_cg, &bar_gen)) break;
+    if (s_cg.done) break;
+    al = static_cast<T>(s_cg.alpha);
+    be = static_cast<T>(s_cg.beta);
+    dot = T(0);
+    gam = T(0);
+  }
+  }   // iterations
 
+  if constexpr (CGM == 2) {
+    if (blockIdx.x == 0 && tid == 0) {
+      a.hook.cg[rhs] = s_cg;
+      a.hook.flags[rhs] = 1;
+    }
+    return;
+  }
   grid_dep_launch();   // the next kernel's blocks may take this block's place
   if constexpr (CG) hook_finish_cg(a.hook, a.cgv.gpartials, rhs, dot, gam, &s_cg);
   else if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, dot, hpre, &s_cg);

@@ -120,10 +120,11 @@ class HDG:
                     "hdg_set_operator_variant")
 
     def set_cg_variant(self, variant):
-        """Inner CG iteration: 'fused' (one tile-kernel launch per iteration,
-        the default with the tile operator) or 'two_kernel' (operator, then
-        the vector update)."""
-        code = {"fused": 0, "two_kernel": 1}[variant]
+        """Inner CG iteration: 'persistent' (the default with the tile
+        operator: the whole inner CG in one cooperative launch), 'fused' (one
+        tile-kernel launch per iteration) or 'two_kernel' (operator, then the
+        vector update)."""
+        code = {"persistent": 0, "fused": 2, "two_kernel": 1}[variant]
         _capi.check(_capi.lib().hdg_set_cg_variant(self._h, code), "hdg_set_cg_variant")
 
     def set_nodal_variant(self, variant):

@@ -275,10 +275,11 @@ def test_polynomial_reproduction_high_degree(p, inner):
 @pytest.mark.parametrize("inner", ["fp32", "fp64"])
 @pytest.mark.parametrize("bc", [(0,) * 6, (1, 0, 1, 0, 1, 0), (0, 1, 1, 1, 0, 1)])
 def test_fused_and_two_kernel_cg_agree(inner, bc):
-    # one kernel per CG iteration (the operator launch applies the previous
-    # update to the face values it reads; each face value has one owner,
-    # also on Neumann sides) against the operator + update kernel pair: both
-    # reach the tolerance on the oracle's residual, with about the same
+    # the fused CG step (the operator launch applies the previous update to
+    # the face values it reads; each face value has one owner, also on
+    # Neumann sides), as one persistent cooperative launch per inner solve and
+    # as one launch per iteration, against the operator + update kernel pair:
+    # all reach the tolerance on the oracle's residual, with about the same
     # iteration count (same iterates in exact arithmetic)
     from paper_2007_11891_gb300 import HDG
     ne, p, lam = (5, 4, 3), 4, 0.7
@@ -286,14 +287,20 @@ def test_fused_and_two_kernel_cg_agree(inner, bc):
     pr = Problem(ne, grid, bc, p, 25.0, lam)
     f = hdg_inputs.gaussian(pr.mesh.n_elem * (p + 1) ** 3, 24)
     out = {}
-    for variant in ("fused", "two_kernel"):
+    for variant in ("persistent", "fused", "two_kernel"):
         h = HDG(ne, grid, bc, p, 25.0)
         h.set_cg_variant(variant)
         tr, u, info = h.solve(torch.tensor(f, device="cuda"), lam, tol=1e-10, inner=inner)
         assert info[0]["status"] == "OK"
         assert _oracle_residual(pr, tr.cpu().numpy(), f=f) <= 1e-10
         out[variant] = (info[0]["iterations"], u)
-    it_f, it_t = out["fused"][0], out["two_kernel"][0]
-    assert abs(it_f - it_t) <= max(3, 0.05 * it_t), (it_f, it_t)
+    it_t = out["two_kernel"][0]
     ref = out["two_kernel"][1].abs().max().item()
-    assert (out["fused"][1] - out["two_kernel"][1]).abs().max().item() <= 1e-8 * ref
+    for variant in ("persistent", "fused"):
+        it_f = out[variant][0]
+        assert abs(it_f - it_t) <= max(3, 0.05 * it_t), (variant, it_f, it_t)
+        assert (out[variant][1] - out["two_kernel"][1]).abs().max().item() <= 1e-8 * ref
+    # the persistent and the per-launch fused step run the same arithmetic in
+    # the same order: the same iterations, bitwise the same solution
+    assert out["persistent"][0] == out["fused"][0]
+    assert torch.equal(out["persistent"][1], out["fused"][1])
