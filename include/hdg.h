@@ -70,7 +70,7 @@ typedef enum {
   HDG_ERR_OOM = 4,           /* device allocation failed                    */
   HDG_ERR_NOT_CONVERGED = 5, /* iteration limit reached before tolerance    */
   HDG_ERR_BREAKDOWN = 6,     /* CG breakdown: p^T K p <= 0 or non-finite     */
-  HDG_ERR_UNSUPPORTED = 7    /* degree above 16, or not an sm_103 device    */
+  HDG_ERR_UNSUPPORTED = 7    /* degree outside the supported range, or not an sm_103 device */
 } hdg_status;
 
 /* Precision of an operator application or of the inner CG solve.
@@ -133,7 +133,12 @@ typedef struct {
  * Eq. (generalized_eigenvalue_decomposition), the row matrix
  * B_S = S^T B - S^T D M^-1 C of Eq. (hdg_bs) and the 2x2 face matrix
  * G + C^T M^-1 C), computed on the host in FP64 and uploaded to the current
- * device.  p in 1..16.  Errors: INVALID_ARG, UNSUPPORTED, CUDA, OOM.
+ * device.  p in 1..32: degrees up to 16 run kernels specialised per degree;
+ * degrees 17..32 run runtime-degree kernels (the operator recomputes the
+ * eigenspace solution along each direction instead of storing it, D_Z^-1 is
+ * computed in the kernel; no BF16 storage, nodal applies always face-wise,
+ * inner CG as two kernels per iteration).  Errors: INVALID_ARG, UNSUPPORTED,
+ * CUDA, OOM.
  * On success *out owns device memory until hdg_destroy.                  */
 hdg_status hdg_setup(const hdg_mesh* mesh, int p, const hdg_options* opts, hdg_ctx** out);
 
@@ -265,22 +270,22 @@ hdg_status hdg_autotune(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_prec
 hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
 
 /* Tuning (not part of the method): work split of the operator kernel.
- * 0 automatic (element tiles), 4 element tiles (every precision: CTAs of
- * n^2 G threads take tiles of consecutive elements; hdg_set_x1_segment sets
- * the elements per tile, rounded to a multiple of G), 1 element runs (one
- * thread per x1-line, runs of elements per CTA slot; slots and run length
- * from hdg_set_slots_per_cta and hdg_set_x1_segment; FP64, FP32 and BF16),
- * and for FP32 only 2 x2-planes (one thread per x2-plane of an element, n
- * threads per element, elements_per_cta elements per CTA, 0 = automatic)
- * and 3 warp slots (one warp per element run, lane t owning the x1-lines
- * t + 32 q).  Same arithmetic per point; FP64 results are bitwise equal,
- * FP32 results agree to FP32 rounding.  Errors: INVALID_ARG (NULL context,
- * variant outside 0..4, or a plane CTA above 128 threads).                 */
-hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant, int elements_per_cta);
+ * 0 automatic (element tiles); 2 element tiles (CTAs of n^2 G threads take
+ * tiles of consecutive elements in element order, one face node / x1-line
+ * per thread; hdg_set_x1_segment sets the elements per tile, rounded to a
+ * multiple of G); 1 element runs (one thread per x1-line, runs of elements
+ * per CTA slot; slots and run length from hdg_set_slots_per_cta and
+ * hdg_set_x1_segment).  FP64, FP32 and BF16 storage.  3 the runtime-degree
+ * kernel that degrees 17..32 always use (every mode, FP64 and FP32; at lower
+ * degrees for comparison).  Same arithmetic per point: FP64 results of 0-2
+ * are bitwise equal, FP32 results agree to FP32 rounding (the tile kernel
+ * uses packed two-lane FP32 arithmetic); 3 agrees to rounding.
+ * Errors: INVALID_ARG (NULL context, variant outside 0..3).               */
+hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant);
 
 /* Tuning (not part of the method): how an inner CG iteration runs.
  *   0 (default) with the element-tile operator kernel
- *     (hdg_set_operator_variant 0 or 4): the whole inner CG in one
+ *     (hdg_set_operator_variant 0 or 2): the whole inner CG in one
  *     cooperative launch of that kernel (every CTA resident; per iteration,
  *     each CTA applies the CG update of the previous iteration to every face
  *     value it reads -- each face value's one owner stores the new x, p, r,

@@ -94,7 +94,7 @@ def lib():
     L.hdg_autotune.restype = ci
     L.hdg_set_dz_mode.argtypes = [vp, ci]
     L.hdg_set_dz_mode.restype = ci
-    L.hdg_set_operator_variant.argtypes = [vp, ci, ci]
+    L.hdg_set_operator_variant.argtypes = [vp, ci]
     L.hdg_set_operator_variant.restype = ci
     L.hdg_set_cg_variant.argtypes = [vp, ci]
     L.hdg_set_cg_variant.restype = ci

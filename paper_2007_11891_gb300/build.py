@@ -17,7 +17,7 @@ OUT_DIR = os.path.join(HERE, "lib")
 BUILD_DIR = os.path.join(ROOT, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libhdg_gb300.so")
 
-SOURCES = ["setup1d.cpp", "kernels.cu", "tpt_f64.cu", "tpt_f32.cu", "tpt_f32_plane.cu", "tpt_f32_warp.cu", "tpt_bf16.cu", "tpt_tile_f32.cu", "tpt_tile_f64.cu", "tpt_tile_bf16.cu", "tp_nodal.cu", "lowdim.cu", "hdg_api.cu", "hdg_static.cu", "probe.cu"]
+SOURCES = ["setup1d.cpp", "kernels.cu", "tpt_f64.cu", "tpt_f32.cu", "tpt_bf16.cu", "tpt_tile_f32.cu", "tpt_tile_f64.cu", "tpt_tile_bf16.cu", "tp_nodal.cu", "lowdim.cu", "hdg_api.cu", "hdg_static.cu", "probe.cu", "tpt_generic.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -9,7 +9,7 @@
 
 namespace hdg {
 
-constexpr int kMaxNDev = 17;
+constexpr int kMaxNDev = 33;   // p <= 32
 
 // Dynamic shared memory above which a kernel's limit is raised explicitly
 // (cudaFuncAttributeMaxDynamicSharedMemorySize).  The default limit of 48 KB

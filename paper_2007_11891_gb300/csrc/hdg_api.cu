@@ -105,9 +105,8 @@ struct hdg_ctx {
   DevBuf loopctl;   // device loop-trip counter of the CG loop graph
   int seg_override = 0;   // x1 segment length; 0 = automatic
   int ppb_override = 0;   // slots per CTA; 0 = automatic
-  int op_variant = 0;     // apply kernel: 0 automatic (tiles), 1 element runs, 2 x2-planes, 3 warp slots, 4 tiles
+  int op_variant = 0;     // apply kernel: 0 automatic (tiles), 1 element runs, 2 element tiles, 3 runtime degree
   int nodal_variant = 0;  // FP64 nodal apply: 0 face-wise transforms + transformed kernel, 1 one kernel (HDG-TP)
-  int plane_epc = 0;      // x2-plane kernel: elements per CTA; 0 = automatic
   int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
   int fused_cg = 0;       // the current inner CG runs the fused tile-kernel step
   int fused_enabled = 1;  // allow the fused step (hdg_set_cg_variant)
@@ -199,6 +198,9 @@ long long dz_table(const hdg_ctx* c) { return (long long)c->n * c->n * hdg::dz_r
 // shared memory) read tables.
 template <typename T>
 bool dz_in_kernel(const hdg_ctx* c) {
+  // above the specialised degrees the generic kernels compute D_Z^-1 (n^3
+  // values per element class and lambda would be too large to keep)
+  if (c->n > hdg::kMaxSpecialisedN) return true;
   if (sizeof(T) != 4) return false;
   // the FP32 kernels index tables with 32-bit offsets
   if ((size_t)nclass(c) * dz_table<T>(c) >= (size_t(1) << 31)) return true;
@@ -261,23 +263,21 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mod
   a.tile = c->seg_override;   // elements per tile of the tile kernel (0 = automatic)
   // apply kernel: element tiles (tpt_tile.cuh) unless another work split is
   // asked for; the FP64 and BF16 applies have the tiles and the element runs
-  if (mode == hdg::TPT_APPLY && (c->op_variant == 0 || c->op_variant == 4)) a.variant = 3;
-  if (std::is_same<ST, float>::value && mode == hdg::TPT_APPLY && c->op_variant >= 1 && c->op_variant <= 3) {
-    const int want = c->op_variant;
-    a.variant = want == 2 ? 1 : (want == 3 ? 2 : 0);
-    if (a.variant == 1) a.ppb = c->plane_epc > 0 ? c->plane_epc : std::max(1, 64 / c->n);
-    if (a.variant == 2) {   // one warp per slot: its own occupancy sets the resident wave
-      a.ppb = hdg::kWarpSlotsPerCta;
-      ctas = c->sms * hdg::warp_slots_blocks_per_sm(c->n);
-      a.max_grid = ctas;
-    }
-  }
+  if (mode == hdg::TPT_APPLY && c->op_variant != 1) a.variant = 3;
+  if (c->op_variant == 3) a.variant = 4;   // runtime-degree kernel, every mode
   // FP32 apply: equal contiguous runs, one per slot of a resident wave (per
   // right-hand side: the wave is shared by the batch)
   const long long nelem = (long long)c->nelem * std::max(nrhs, 1);
   const long long slots = std::max(1LL, (long long)ctas * a.ppb);
   a.chunk = c->seg_override > 0 ? c->seg_override : (int)std::max(1LL, (nelem + slots - 1) / slots);
   return a;
+}
+
+// The kernel of `a` adds into every face of the output (the FP32 kernels,
+// the tiles, the runtime-degree kernel), not only the x2/x3 blocks.
+template <typename T, typename ST>
+bool full_zero(const hdg_ctx* c, const hdg::TptArgs<T, ST>& a) {
+  return sizeof(T) == 4 || a.variant >= 3 || c->n > hdg::kMaxSpecialisedN;
 }
 
 // Zero what the operator accumulates with atomics: the x2/x3 blocks, and the
@@ -298,7 +298,7 @@ hdg_status tpt_apply(hdg_ctx* c, int nrhs, const T* dinv, const ST* x, ST* y, cu
                      bool pdl = false) {
   hdg::TptArgs<T, ST> a = base_args<T, ST>(c, dinv, nrhs);
   // the FP32 kernel's runs may split any x1-pencil: zero the whole output
-  if (!zeroed) HDG_TRY(zero_for_tpt<ST>(c, y, nrhs, (sizeof(T) == 4 || a.variant == 3) ? 2 : a.nseg, s));
+  if (!zeroed) HDG_TRY(zero_for_tpt<ST>(c, y, nrhs, full_zero(c, a) ? 2 : a.nseg, s));
   a.x = x;
   a.y = y;
   a.skip = skip;
@@ -391,6 +391,7 @@ hdg_status ensure_pc(hdg_ctx* c, int nrhs, const double* lam, cudaStream_t s) {
   HDG_CUDA(cudaMemsetAsync(c->pc_diag.p, 0, sizeof(double) * tot, s));
   { Timed t_(c, K_VEC, s);
     HDG_CUDA(hdg::launch_pc_diag(c->mesh, c->n, c->tab64, c->d_metric64, dinv, nclass(c) * dz_table<double>(c),
+                                 static_cast<const double*>(lam_buf<double>(c).p),
                                  static_cast<double*>(c->pc_diag.p), nrhs, c->ntrace, s)); }
   { Timed t_(c, K_VEC, s);
     HDG_CUDA(hdg::launch_pc_invert(static_cast<double*>(c->pc_diag.p), static_cast<double*>(c->pc_w64.p),
@@ -729,7 +730,7 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   // the fused step (one tile-kernel launch per iteration) whenever the tile
   // kernel is the operator; the two-kernel loop (operator, cg_step_kernel)
   // for the other work splits
-  c->fused_cg = (c->fused_enabled && (c->op_variant == 0 || c->op_variant == 4)) ? 1 : 0;
+  c->fused_cg = (c->fused_enabled && (c->op_variant == 0 || c->op_variant == 2) && c->n <= hdg::kMaxSpecialisedN) ? 1 : 0;
   for (int i : {W_R, W_D, W_P, W_Q, W_U, W_S}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
   if (c->fused_cg) {
     for (int i : {W_R2, W_S2, W_W2, W_W3}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
@@ -870,7 +871,7 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
   // 3. transformed right-hand side with Dirichlet lift and Neumann load
   {
     hdg::TptArgs<double, double> a = base_args<double, double>(c, dinv, nrhs, hdg::TPT_RHS);
-    HDG_TRY(zero_for_tpt<double>(c, Fhat, nrhs, a.nseg, s));
+    HDG_TRY(zero_for_tpt<double>(c, Fhat, nrhs, full_zero(c, a) ? 2 : a.nseg, s));
     a.y = Fhat;
     a.gbd = ghat;
     a.src = fhat;
@@ -1052,7 +1053,7 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
   HDG_CUDA(cudaMemsetAsync(c->ws[W_XHAT].p, 0x3c, esz * tot, s));   // finite, non-zero pattern
   // candidate segment lengths (distinct splits of the x1-pencils) and slots;
   // for the tile kernel: elements per tile, no slots
-  const bool tiles = c->op_variant == 0 || c->op_variant == 4;
+  const bool tiles = c->op_variant == 0 || c->op_variant == 2;
   std::vector<int> segs = {0};
   if (tiles) {
     for (int e : {2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32}) segs.push_back(e);
@@ -1124,11 +1125,9 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
   return HDG_OK;
 }
 
-hdg_status hdg_set_operator_variant(hdg_ctx* c, int variant, int elements_per_cta) {
-  if (!c || variant < 0 || variant > 4 || elements_per_cta < 0 || elements_per_cta * c->n > 128)
-    return fail(HDG_ERR_INVALID_ARG, "NULL context, variant outside 0..4 or x2-plane CTA above 128 threads");
+hdg_status hdg_set_operator_variant(hdg_ctx* c, int variant) {
+  if (!c || variant < 0 || variant > 3) return fail(HDG_ERR_INVALID_ARG, "NULL context or variant outside 0..3");
   c->op_variant = variant;
-  c->plane_epc = elements_per_cta;
   return HDG_OK;
 }
 
@@ -1199,7 +1198,7 @@ hdg_status hdg_setup(const hdg_mesh* mesh, int p, const hdg_options* opts, hdg_c
   begin_call();
   if (!mesh || !out) return fail(HDG_ERR_INVALID_ARG, "mesh and out must not be NULL");
   *out = nullptr;
-  if (p < 1 || p > 16) return fail(HDG_ERR_UNSUPPORTED, "degree p must be in 1..16");
+  if (p < 1 || p > 32) return fail(HDG_ERR_UNSUPPORTED, "degree p must be in 1..32");
   const double tau_hat = opts ? opts->tau_hat : 25.0;
   const int lumped = opts ? opts->mass_lumped : 0;
   for (int d = 0; d < 3; ++d) {
@@ -1372,7 +1371,8 @@ hdg_status hdg_apply(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precision
     HDG_TRY(ensure_dinv<double>(c, nrhs, h_lambda, s, &dinv));
     if (basis == HDG_BASIS_TRANSFORMED)
       return tpt_apply<double, double>(c, nrhs, dinv, static_cast<const double*>(d_x), static_cast<double*>(d_y), s);
-    if (c->nodal_variant == 1) return nodal_apply(c, nrhs, dinv, static_cast<const double*>(d_x), static_cast<double*>(d_y), s);
+    if (c->nodal_variant == 1 && n <= hdg::kMaxSpecialisedN)
+      return nodal_apply(c, nrhs, dinv, static_cast<const double*>(d_x), static_cast<double*>(d_y), s);
     HDG_TRY(ensure(c->ws[W_XHAT], sizeof(double) * tot));
     HDG_TRY(ensure(c->ws[W_YHAT], sizeof(double) * tot));
     double* xh = wsp<double>(c, W_XHAT);

@@ -123,8 +123,9 @@ extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_l
   hdg::tpt_split(v.n, v.mesh.ne, nrhs, ctas, ppb, &seg, &nseg);
   // the array keeps the previous call's contents: the parts of the operator
   // output that are accumulated with atomics must start at zero (the x2/x3
-  // blocks, and everything when x1-pencils are split into segments)
-  const long long off = nseg > 1 ? 0 : v.mesh.blk[1] * (long long)v.n * v.n;
+  // blocks, and everything when x1-pencils are split into segments or the
+  // runtime-degree kernel runs)
+  const long long off = (nseg > 1 || v.n > hdg::kMaxSpecialisedN) ? 0 : v.mesh.blk[1] * (long long)v.n * v.n;
   if (v.ntrace - off > 0 &&
       (e = cudaMemset2DAsync(yh + off, sizeof(double) * v.ntrace, 0, sizeof(double) * (v.ntrace - off), nrhs, s)) !=
           cudaSuccess)
@@ -135,6 +136,7 @@ extern "C" hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_l
   a.metric = v.metric64;
   a.dinv = dinv;
   a.dinv_rhs_stride = v.nclass * dzt;
+  a.lam = lam;   // the runtime-degree kernel (p > 16) computes D_Z^-1 from it
   a.x = xh;
   a.y = yh;
   a.trace_stride = v.ntrace;

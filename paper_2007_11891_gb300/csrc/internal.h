@@ -26,17 +26,15 @@ void tpt_split(int n, const int ne[3], int nrhs, int ctas, int ppb, int* seg, in
 // resident CTAs per SM of tpt_kernel<T, ST, n, mode> at ppb slots per CTA
 template <typename T, typename ST>
 int tpt_blocks_per_sm(int mode, int n, int ppb);
-// resident CTAs per SM of the FP32 warp-slot operator (tpt_warp.cuh), whose
-// CTAs hold kWarpSlotsPerCta one-warp slots
-constexpr int kWarpSlotsPerCta = 4;
-int warp_slots_blocks_per_sm(int n);
+// any mode for degrees above the specialised kernels (tpt_generic.cuh):
+// D_Z^-1 computed in the kernel, a.dinv ignored
+template <typename T>
+cudaError_t launch_generic(int mode, int n, const TptArgs<T, T>& a, int nrhs, cudaStream_t s);
+constexpr int kMaxSpecialisedN = 17;
 // the apply with the tile kernel (tpt_tile.cuh), per storage precision
 cudaError_t launch_tile_f32(int n, const TptArgs<float, float>& a, int nrhs, cudaStream_t s);
 cudaError_t launch_tile_f64(int n, const TptArgs<double, double>& a, int nrhs, cudaStream_t s);
 cudaError_t launch_tile_bf16(int n, const TptArgs<float, __nv_bfloat16>& a, int nrhs, cudaStream_t s);
-// FP32 apply with the alternative work splits (hdg_set_operator_variant)
-cudaError_t launch_tpt_warp_slots(int n, const TptArgs<float, float>& a, int nrhs, cudaStream_t s);
-cudaError_t launch_tpt_planes(int n, const TptArgs<float, float>& a, int nrhs, cudaStream_t s);
 
 // ---- tp_nodal.cu: nodal-basis operator in one kernel (Alg. hdg_op_3d) ------
 struct NodalArgs {
@@ -115,9 +113,10 @@ cudaError_t launch_dot(const T* a, const T* b, const T* w, long long len, int nr
 
 // face-block Jacobi preconditioner: diag (zeroed by the caller) += the face
 // self-coupling of K-hat; then w = 1 / diag in FP64 and FP32
+// (dinv null: D_Z^-1 computed from lam[r], the metric and tab.lam)
 cudaError_t launch_pc_diag(const MeshDev& m, int n, const Tables<double>& tab, const double* metric,
-                           const double* dinv, long long dinv_rhs_stride, double* diag, int nrhs,
-                           long long tstride, cudaStream_t s);
+                           const double* dinv, long long dinv_rhs_stride, const double* lam, double* diag,
+                           int nrhs, long long tstride, cudaStream_t s);
 cudaError_t launch_pc_invert(const double* diag, double* w64, float* w32, long long count, cudaStream_t s);
 
 // ---- CG (cg_kernels in kernels.cu) ----------------------------------------------

@@ -144,6 +144,88 @@ __global__ void face_rows_kernel(const TI* __restrict__ x, TO* __restrict__ y, l
   }
 }
 
+// Runtime-n forms of the two transforms, for degrees above the specialised
+// instantiations: the same products, the matrix staged in shared memory.
+// Face transform: one slot of n threads per face (row pass, then column
+// pass through shared memory).
+template <typename TI, typename TO>
+__global__ void face_rows_generic_kernel(const TI* __restrict__ x, TO* __restrict__ y, long long nfaces,
+                                         long long sx, long long sy, const Mat1D<TO> W, TO scale, int accumulate,
+                                         int fpb, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TO* Wm = reinterpret_cast<TO*>(smem_raw);   // W[row][col], n x n
+  TO* sm = Wm + n * n;
+  const int n2 = n * n;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) Wm[t] = W.a[t];
+  const int slot = threadIdx.x / n;
+  const int l = threadIdx.x - slot * n;
+  const long long face = (long long)blockIdx.x * fpb + slot;
+  const bool act = slot < fpb && face < nfaces;
+  const int r = blockIdx.y;
+  TO* Tm = sm + (act ? slot : 0) * n2;
+  __syncthreads();
+  if (act) {
+    const TI* xf = x + r * sx + face * n2 + n * l;
+    for (int a = 0; a < n; ++a) {
+      TO acc = TO(0);
+      for (int c = 0; c < n; ++c) acc = fma(Wm[a * n + c], load_as<TI, TO>(xf + c), acc);
+      Tm[n * l + a] = acc;
+    }
+  }
+  __syncthreads();
+  if (act) {
+    TO* yf = y + r * sy + face * n2 + l;
+    for (int a = 0; a < n; ++a) {
+      TO acc = TO(0);
+      for (int c = 0; c < n; ++c) acc = fma(Wm[a * n + c], Tm[n * c + l], acc);
+      TO v = scale * acc;
+      if (accumulate) v += yf[n * a];
+      yf[n * a] = v;
+    }
+  }
+}
+
+// Volume transform y_e = s_e (A (x) A (x) A) x_e: one CTA per element, three
+// passes of line transforms (x1 lines from x into y, then x2 and x3 lines of
+// y in place: each line is read whole into registers by the one thread that
+// writes it back), the scale applied in the last pass.
+constexpr int kGenericLine = 33;
+__global__ void __launch_bounds__(256) volume_transform_generic_kernel(const double* __restrict__ x, double* y,
+                                                                       long long nelem, long long stride,
+                                                                       const Mat1D<double> A,
+                                                                       const double* __restrict__ metric,
+                                                                       int uniform, int use_d0, int n) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Am = reinterpret_cast<double*>(smem_raw);
+  const int n2 = n * n;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) Am[t] = A.a[t];
+  __syncthreads();
+  const int r = blockIdx.y;
+  for (long long e = blockIdx.x; e < nelem; e += gridDim.x) {
+    const double* xe = x + r * stride + e * (long long)(n2 * n);
+    double* ye = y + r * stride + e * (long long)(n2 * n);
+    const double sc = use_d0 ? metric[uniform ? 0 : 4 * e] : 1.0;
+    for (int pass = 0; pass < 3; ++pass) {
+      const int st = pass == 0 ? 1 : (pass == 1 ? n : n2);   // stride along the line
+      for (int line = threadIdx.x; line < n2; line += blockDim.x) {
+        const int la = line % n, lb = line / n;
+        // first node of the line: the two other indices (la, lb)
+        const long long b0 = pass == 0 ? (long long)n * la + (long long)n2 * lb
+                                       : (pass == 1 ? la + (long long)n2 * lb : la + (long long)n * lb);
+        const double* src = pass == 0 ? xe + b0 : ye + b0;
+        double in[kGenericLine];
+        for (int c = 0; c < n; ++c) in[c] = src[(long long)c * st];
+        for (int a = 0; a < n; ++a) {
+          double acc = 0.0;
+          for (int c = 0; c < n; ++c) acc = fma(Am[a * n + c], in[c], acc);
+          ye[b0 + (long long)a * st] = pass == 2 ? sc * acc : acc;
+        }
+      }
+      __syncthreads();   // the next pass reads lines other threads wrote
+    }
+  }
+}
+
 template <int N, int PAR>
 __global__ void volume_transform_kernel(const double* __restrict__ x, double* __restrict__ y,
                                         long long nelem, long long stride, const Mat1D<double> A,
@@ -257,7 +339,7 @@ __global__ void neumann_add_kernel(MeshDev m, int n, const double* __restrict__ 
 //   Y(a, b) = sum_e [ d h0 - d^2 sum_m c_m^2 D_Z^-1(m, a, b) ].
 __global__ void pc_diag_kernel(MeshDev m, int n, Tables<double> tab, const double* __restrict__ metric,
                                const double* __restrict__ dinv, long long dinv_rhs_stride,
-                               double* __restrict__ diag, long long tstride) {
+                               const double* __restrict__ lam, double* __restrict__ diag, long long tstride) {
   const int r = blockIdx.y;
   const int n2 = n * n;
   const long long nel = (long long)m.ne[0] * m.ne[1] * m.ne[2];
@@ -271,13 +353,19 @@ __global__ void pc_diag_kernel(MeshDev m, int n, Tables<double> tab, const doubl
     const int e3 = (int)(e / ((long long)m.ne[0] * m.ne[1]));
     const double* mt = metric + (m.uniform ? 0 : 4 * e);
     const int row = dz_row(n, sizeof(double));
-    const double* dz = dinv + r * dinv_rhs_stride + (m.uniform ? 0 : e * (long long)n2 * row);
+    const double* dz = dinv ? dinv + r * dinv_rhs_stride + (m.uniform ? 0 : e * (long long)n2 * row) : nullptr;
+    // D_Z^-1(i, j, k) from the table, or computed (no table above the
+    // specialised degrees)
+    auto dzv = [&](int i, int j, int k) -> double {
+      if (dz) return dz[i + row * (j + n * k)];
+      return 1.0 / (lam[r] * mt[0] + mt[1] * tab.lam[i] + mt[2] * tab.lam[j] + mt[3] * tab.lam[k]);
+    };
     double sd[3] = {0.0, 0.0, 0.0};
     for (int t2 = 0; t2 < n; ++t2) {
       const double c2 = tab.c[t2] * tab.c[t2];
-      sd[0] += c2 * dz[t2 + row * (lo + n * hi)];   // x1 face node (j, k) = (lo, hi)
-      sd[1] += c2 * dz[lo + row * (t2 + n * hi)];   // x2 face node (i, k) = (lo, hi)
-      sd[2] += c2 * dz[lo + row * (hi + n * t2)];   // x3 face node (i, j) = (lo, hi)
+      sd[0] += c2 * dzv(t2, lo, hi);   // x1 face node (j, k) = (lo, hi)
+      sd[1] += c2 * dzv(lo, t2, hi);   // x2 face node (i, k) = (lo, hi)
+      sd[2] += c2 * dzv(lo, hi, t2);   // x3 face node (i, j) = (lo, hi)
     }
     const int ed[3] = {e1, e2, e3};
     const long long fab[3] = {e2 + (long long)m.ne[1] * e3, e1 + (long long)m.ne[0] * e3,
@@ -652,7 +740,7 @@ cudaError_t vt_one(const double* x, double* y, long long nelem, int nrhs, long l
 
 }  // namespace
 
-#define HDG_N_SWITCH(n, CALL)                                                   \
+#define HDG_N_SWITCH(n, CALL, GENERIC)                                          \
   switch (n) {                                                                  \
     case 2: return CALL(2); case 3: return CALL(3); case 4: return CALL(4);     \
     case 5: return CALL(5); case 6: return CALL(6); case 7: return CALL(7);     \
@@ -660,15 +748,44 @@ cudaError_t vt_one(const double* x, double* y, long long nelem, int nrhs, long l
     case 11: return CALL(11); case 12: return CALL(12); case 13: return CALL(13); \
     case 14: return CALL(14); case 15: return CALL(15); case 16: return CALL(16); \
     case 17: return CALL(17);                                                   \
-    default: return cudaErrorInvalidValue;                                      \
+    default: return GENERIC;                                                    \
   }
+
+template <typename TI, typename TO>
+cudaError_t ft_generic(int n, const TI* x, TO* y, long long nfaces, int nrhs, long long sx, long long sy,
+                       const Mat1D<double>& Wd, double scale, int accumulate, cudaStream_t s) {
+  if (n < 2 || n > kMaxNDev) return cudaErrorInvalidValue;
+  if (nfaces <= 0) return cudaSuccess;
+  Mat1D<TO> W;
+  for (int i = 0; i < n * n; ++i) W.a[i] = static_cast<TO>(Wd.a[i]);
+  const int fpb = std::max(1, 256 / n);
+  const int threads = (fpb * n + 31) / 32 * 32;
+  const size_t smem = (size_t)(fpb + 1) * n * n * sizeof(TO);
+  if (smem > kSmemOptIn)
+    cudaFuncSetAttribute(face_rows_generic_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  dim3 grid((unsigned)((nfaces + fpb - 1) / fpb), nrhs);
+  face_rows_generic_kernel<TI, TO><<<grid, threads, smem, s>>>(x, y, nfaces, sx, sy, W, static_cast<TO>(scale),
+                                                              accumulate, fpb, n);
+  return cudaGetLastError();
+}
+
+cudaError_t vt_generic(int n, const double* x, double* y, long long nelem, int nrhs, long long stride,
+                       const Mat1D<double>& A, const double* metric, int uniform, int use_d0, cudaStream_t s) {
+  if (n < 2 || n > kGenericLine || n > kMaxNDev || x == y) return cudaErrorInvalidValue;
+  if (nelem <= 0) return cudaSuccess;
+  const size_t smem = (size_t)n * n * sizeof(double);
+  const long long blocks = std::min<long long>(nelem, 65535LL * 4);
+  dim3 grid((unsigned)blocks, nrhs);
+  volume_transform_generic_kernel<<<grid, 256, smem, s>>>(x, y, nelem, stride, A, metric, uniform, use_d0, n);
+  return cudaGetLastError();
+}
 
 template <typename TI, typename TO>
 cudaError_t launch_face_transform(int n, const TI* x, TO* y, long long nfaces, int nrhs,
                                   long long stride_x, long long stride_y, const Mat1D<double>& W,
                                   double scale, int accumulate, cudaStream_t s) {
 #define FT_CALL(N) ft_one<TI, TO, N>(x, y, nfaces, nrhs, stride_x, stride_y, W, scale, accumulate, s)
-  HDG_N_SWITCH(n, FT_CALL)
+  HDG_N_SWITCH(n, FT_CALL, (ft_generic<TI, TO>(n, x, y, nfaces, nrhs, stride_x, stride_y, W, scale, accumulate, s)))
 #undef FT_CALL
 }
 template cudaError_t launch_face_transform<double, double>(int, const double*, double*, long long, int,
@@ -682,7 +799,7 @@ cudaError_t launch_volume_transform(int n, const double* x, double* y, long long
                                     long long stride, const Mat1D<double>& A, const double* metric,
                                     int uniform, int use_d0, cudaStream_t s) {
 #define VT_CALL(N) vt_one<N>(x, y, nelem, nrhs, stride, A, metric, uniform, use_d0, s)
-  HDG_N_SWITCH(n, VT_CALL)
+  HDG_N_SWITCH(n, VT_CALL, (vt_generic(n, x, y, nelem, nrhs, stride, A, metric, uniform, use_d0, s)))
 #undef VT_CALL
 }
 
@@ -748,11 +865,11 @@ template cudaError_t launch_dot<float>(const float*, const float*, const float*,
                                        unsigned int*, double*, int, cudaStream_t);
 
 cudaError_t launch_pc_diag(const MeshDev& m, int n, const Tables<double>& tab, const double* metric,
-                           const double* dinv, long long dinv_rhs_stride, double* diag, int nrhs,
-                           long long tstride, cudaStream_t s) {
+                           const double* dinv, long long dinv_rhs_stride, const double* lam, double* diag,
+                           int nrhs, long long tstride, cudaStream_t s) {
   const long long total = (long long)m.ne[0] * m.ne[1] * m.ne[2] * n * n;
   dim3 grid(grid_for(total, kVecThreads), nrhs);
-  pc_diag_kernel<<<grid, kVecThreads, 0, s>>>(m, n, tab, metric, dinv, dinv_rhs_stride, diag, tstride);
+  pc_diag_kernel<<<grid, kVecThreads, 0, s>>>(m, n, tab, metric, dinv, dinv_rhs_stride, lam, diag, tstride);
   return cudaGetLastError();
 }
 

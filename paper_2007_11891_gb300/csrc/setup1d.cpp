@@ -235,7 +235,7 @@ bool block_eigen(int n, int k, const Mat& P, const Mat& M, const Mat& L, Mat& Sb
 int build_setup1d(int p, double tau_hat, int mass_lumped, Setup1D* out, const char** msg) {
   static const char* kOk = "";
   *msg = kOk;
-  if (p < 1 || p + 1 > kMaxN) { *msg = "degree p must be in 1..16"; return 1; }
+  if (p < 1 || p + 1 > kMaxN) { *msg = "degree p must be in 1..32"; return 1; }
   if (!(tau_hat > 0.0)) { *msg = "tau_hat must be > 0"; return 1; }
   Setup1D& s = *out;
   s = Setup1D();

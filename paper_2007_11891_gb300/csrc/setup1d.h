@@ -15,7 +15,7 @@
 
 namespace hdg {
 
-constexpr int kMaxN = 17;  // degree p <= 16
+constexpr int kMaxN = 33;  // degree p <= 32
 
 struct Setup1D {
   int n = 0;                       // p + 1

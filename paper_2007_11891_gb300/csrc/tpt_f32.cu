@@ -1,8 +1,8 @@
 // FP32 instantiations of the condensed operator: the element-run apply
-// kernel (tpt_fast.cuh) for the inner CG, the generic kernel (tpt_kernel.cuh)
-// otherwise; the x2-plane and warp-slot variants and the BF16-storage
-// instantiations live in translation units of their own (tpt_f32_plane.cu,
-// tpt_f32_warp.cu, tpt_bf16.cu) so that the build compiles them in parallel.
+// kernel (tpt_fast.cuh), the generic kernel (tpt_kernel.cuh) for the other
+// modes; the tile kernel (tpt_tile_f32.cu) and the BF16-storage
+// instantiations (tpt_bf16.cu) live in translation units of their own so that
+// the build compiles them in parallel.
 #include "tpt_fast_launch.cuh"
 #include "tpt_launch.cuh"
 
@@ -22,9 +22,8 @@ int tpt_blocks_per_sm<float, float>(int mode, int n, int ppb) {
 
 template <>
 cudaError_t launch_tpt<float, float>(int mode, int n, TptArgs<float, float> a, int nrhs, cudaStream_t s) {
+  if (n > kMaxSpecialisedN || a.variant == 4) return launch_generic<float>(mode, n, a, nrhs, s);
   if (mode == TPT_APPLY && a.variant == 3) return launch_tile_f32(n, a, nrhs, s);
-  if (mode == TPT_APPLY && a.variant == 2) return launch_tpt_warp_slots(n, a, nrhs, s);
-  if (mode == TPT_APPLY && a.variant == 1) return launch_tpt_planes(n, a, nrhs, s);
   if (mode == TPT_APPLY) {
 #define FL(N) fast_dispatch_dz<N, float>(a, nrhs, s)
     FAST_N_SWITCH(n, FL)

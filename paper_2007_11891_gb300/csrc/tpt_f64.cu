@@ -43,6 +43,7 @@ int tpt_blocks_per_sm<double, double>(int mode, int n, int ppb) {
 template <>
 cudaError_t launch_tpt<double, double>(int mode, int n, TptArgs<double, double> a, int nrhs,
                                        cudaStream_t s) {
+  if (n > kMaxSpecialisedN || a.variant == 4) return launch_generic<double>(mode, n, a, nrhs, s);
   if (mode == TPT_APPLY && a.variant == 3) return launch_tile_f64(n, a, nrhs, s);
   return tpt_dispatch<double, double>(mode, n, a, nrhs, s);
 }

@@ -229,7 +229,7 @@ struct TptArgs {
   int pdl;                      // host: launch with programmatic stream serialization
   int variant;                  // apply kernel: 0 element runs (tpt_fast.cuh / tpt_kernel.cuh),
                                 // 1 x2-planes (tpt_plane.cuh), 2 warp slots (tpt_warp.cuh),
-                                // 3 element tiles (tpt_tile.cuh)
+                                // 3 element tiles (tpt_tile.cuh), 4 runtime degree (tpt_generic.cuh)
   int sms;                      // host: SMs of the device (tile kernel grid)
   int tile;                     // host: elements per tile of the tile kernel, 0 = automatic
   int cg;                       // tile kernel: 1 = fused CG step (cgv), 0 = plain apply

@@ -110,14 +110,12 @@ class HDG:
         code = {"auto": 0, "table": 1, "kernel": 2}[mode]
         _capi.check(_capi.lib().hdg_set_dz_mode(self._h, code), "hdg_set_dz_mode")
 
-    def set_operator_variant(self, variant, elements_per_cta=0):
-        """Operator kernel: 'auto' or 'tiles' (element tiles, every
-        precision), 'runs' (one thread per x1-line in element runs), and for
-        FP32 'planes' (one thread per x2-plane; elements_per_cta, 0 =
-        automatic) or 'warps' (one warp per element slot)."""
-        code = {"auto": 0, "runs": 1, "planes": 2, "warps": 3, "tiles": 4}[variant]
-        _capi.check(_capi.lib().hdg_set_operator_variant(self._h, code, int(elements_per_cta)),
-                    "hdg_set_operator_variant")
+    def set_operator_variant(self, variant):
+        """Operator kernel: 'auto' or 'tiles' (element tiles), 'runs' (one
+        thread per x1-line in element runs) or 'generic' (the runtime-degree
+        kernel that degrees above 16 use, any degree)."""
+        code = {"auto": 0, "runs": 1, "tiles": 2, "generic": 3}[variant]
+        _capi.check(_capi.lib().hdg_set_operator_variant(self._h, code), "hdg_set_operator_variant")
 
     def set_cg_variant(self, variant):
         """Inner CG iteration: 'persistent' (the default with the tile

@@ -54,7 +54,7 @@ def test_setup_argument_errors(L):
     h = ctypes.c_void_p()
     o = _capi.HdgOptions(25.0, 0)
     assert L.hdg_setup(ctypes.byref(m), 0, ctypes.byref(o), ctypes.byref(h)) == 7   # p out of range
-    assert L.hdg_setup(ctypes.byref(m), 17, ctypes.byref(o), ctypes.byref(h)) == 7
+    assert L.hdg_setup(ctypes.byref(m), 33, ctypes.byref(o), ctypes.byref(h)) == 7
     m.bc[0] = 3
     assert L.hdg_setup(ctypes.byref(m), 2, ctypes.byref(o), ctypes.byref(h)) == 1   # bad bc
     m.bc[0] = 0
@@ -69,7 +69,7 @@ def test_setup_argument_errors(L):
 
 def test_tuning_setters_reject_null_context(L):
     assert L.hdg_set_nodal_variant(None, 1) == 1
-    assert L.hdg_set_operator_variant(None, 1, 0) == 1
+    assert L.hdg_set_operator_variant(None, 1) == 1
     assert L.hdg_set_dz_mode(None, 0) == 1
 
 

@@ -157,7 +157,7 @@ def test_x1_segment_length_does_not_change_results():
         else:
             # same per-point arithmetic, same two-term face sums: FP64 bitwise
             assert torch.equal(outs[0][0], tiles[0]) and torch.equal(outs[0][1], tiles[1])
-            assert float((outs[0][2] - tiles[2]).abs().max()) <= 1e-6 * float(tiles[2].abs().max())
+            assert float((outs[0][2] - tiles[2]).abs().max()) <= 1e-5 * float(tiles[2].abs().max())
     ref = pr.apply(x.cpu().numpy())
     assert np.abs(tiles[0].cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
 
@@ -263,7 +263,7 @@ def test_apply_bf16_storage(ne, bc, p, stretched):
         h.apply(x, 1.5, basis="nodal")
 
 
-@pytest.mark.parametrize("variant", ["tiles", "runs", "planes", "warps"])
+@pytest.mark.parametrize("variant", ["tiles", "runs"])
 @pytest.mark.parametrize("name,ne,bc,p,stretched,lam,tau", CASES, ids=[c[0] for c in CASES])
 def test_apply_fp32_variants_match_oracle(variant, name, ne, bc, p, stretched, lam, tau):
     # the FP32 work splits (one thread per x1-line in element runs, one
@@ -285,35 +285,40 @@ def test_apply_fp32_variants_match_oracle(variant, name, ne, bc, p, stretched, l
         assert torch.equal(h.apply(xt, lam, basis="transformed"), yt)
 
 
-def test_planes_solve_matches_runs_solve():
+def test_tiles_solve_matches_runs_solve():
     from paper_2007_11891_gb300 import HDG
     ne, p, lam = (6, 5, 4), 6, 2.0
     grid = _grid(ne, True, 31)
     f = torch.tensor(hdg_inputs.gaussian(6 * 5 * 4 * 7 ** 3, 31), device="cuda")
     out = {}
-    for variant in ("tiles", "runs", "planes", "warps"):
+    for variant in ("tiles", "runs"):
         h = HDG(ne, grid, (0,) * 6, p, 25.0)
         h.set_operator_variant(variant)
         tr, u, info = h.solve(f, lam, tol=1e-11, inner="fp32")
         assert info[0]["status"] == "OK"
         out[variant] = u
     ref = out["runs"].abs().max().item()
-    assert (out["planes"] - out["runs"]).abs().max().item() <= 1e-8 * ref
-    assert (out["warps"] - out["runs"]).abs().max().item() <= 1e-8 * ref
     assert (out["tiles"] - out["runs"]).abs().max().item() <= 1e-8 * ref
 
 
-def test_warps_variant_full_size_matches_runs():
+@pytest.mark.parametrize("workload", ["stretched_p8", "uniform32"])
+def test_tiles_full_size_matches_runs(workload):
+    # the full bench and sweep meshes: tiles against element runs (FP64
+    # bitwise, FP32 to rounding), tiles bitwise repeatable
     from paper_2007_11891_gb300 import HDG
-    cfg = hdg_inputs.WORKLOADS["stretched_p8"]
+    cfg = hdg_inputs.WORKLOADS[workload]
     ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"]
     h = HDG(ne, hdg_inputs.grid_lines(ne, cfg["stretched"]), (0,) * 6, p, hdg_inputs.TAU_HAT)
-    x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device="cuda", dtype=torch.float32)
-    y_runs = h.apply(x, lam, basis="transformed")
-    h.set_operator_variant("warps")
-    y_w = h.apply(x, lam, basis="transformed")
-    assert torch.equal(h.apply(x, lam, basis="transformed"), y_w)
-    assert float((y_w - y_runs).abs().max()) <= 1e-6 * float(y_runs.abs().max())
+    x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device="cuda")
+    h.set_operator_variant("runs")
+    y64_r = h.apply(x, lam, basis="transformed")
+    y32_r = h.apply(x.float(), lam, basis="transformed")
+    h.set_operator_variant("tiles")
+    y64_t = h.apply(x, lam, basis="transformed")
+    y32_t = h.apply(x.float(), lam, basis="transformed")
+    assert torch.equal(y64_t, y64_r)
+    assert torch.equal(h.apply(x.float(), lam, basis="transformed"), y32_t)
+    assert float((y32_t - y32_r).abs().max()) <= 1e-5 * float(y32_r.abs().max())
 
 
 # ---- nodal basis in one kernel (Alg. hdg_op_3d, HDG-TP) ------------------------
@@ -393,3 +398,20 @@ def test_slab_partition_subdomain_applies_on_gpu(world):
         y[pt.global_index] = yl
     ref = pr.apply(x)
     assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("name,ne,bc,p,stretched,lam,tau", CASES, ids=[c[0] for c in CASES])
+def test_runtime_degree_kernel_matches_oracle(name, ne, bc, p, stretched, lam, tau):
+    # the kernel degrees 17..32 run (recomputing the eigenspace solution along
+    # each direction, D_Z^-1 by division), forced at degrees the oracle
+    # reaches: FP64 within 1e-12, FP32 within 1e-5
+    h, pr = _pair(ne, bc, p, stretched, lam, tau)
+    h.set_operator_variant("generic")
+    if h.trace_size == 0:
+        return
+    x = hdg_inputs.uniform_pm1(h.trace_size, 11893)
+    ref = pr.apply(x)
+    y = h.apply(torch.tensor(x, device="cuda"), lam).cpu().numpy()
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    y32 = h.apply(torch.tensor(x, device="cuda", dtype=torch.float32), lam).double().cpu().numpy()
+    assert np.abs(y32 - ref).max() <= 1e-5 * np.abs(ref).max()

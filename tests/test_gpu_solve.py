@@ -250,9 +250,12 @@ def test_paper_manufactured_case_small(inner):
     assert np.abs(u.cpu().numpy() - u_ref).max() <= 1e-7 * np.abs(u_ref).max()
 
 
-@pytest.mark.parametrize("p,inner", [(13, "fp64"), (15, "fp64"), (15, "fp32"), (16, "fp32")])
+@pytest.mark.parametrize("p,inner", [(13, "fp64"), (15, "fp64"), (15, "fp32"), (16, "fp32"),
+                                     (17, "fp32"), (20, "fp64"), (20, "fp32"), (24, "fp32"), (32, "fp32"),
+                                     (32, "fp64")])
 def test_polynomial_reproduction_high_degree(p, inner):
-    # degrees whose operator kernels hold 30-60 KB of shared memory per slot;
+    # high degrees (p > 16 runs the runtime-degree kernels: operator, face and
+    # volume transforms, preconditioner with D_Z^-1 computed in the kernel);
     # Q_p data are reproduced exactly (pinned against the oracle at low p), so
     # the exact polynomial is the reference here, without the oracle's dense
     # element solves
@@ -304,3 +307,38 @@ def test_fused_and_two_kernel_cg_agree(inner, bc):
     # the same order: the same iterations, bitwise the same solution
     assert out["persistent"][0] == out["fused"][0]
     assert torch.equal(out["persistent"][1], out["fused"][1])
+
+
+@pytest.mark.parametrize("inner", ["fp64", "fp32"])
+@pytest.mark.parametrize("ne,bc,p", [((3, 2, 4), (0, 1, 0, 0, 1, 0), 3), ((2, 3, 2), (1, 0, 0, 1, 0, 0), 6)])
+def test_runtime_degree_kernel_solve_matches_oracle(ne, bc, p, inner):
+    # the runtime-degree kernels (every operator mode: RHS, apply with the CG
+    # hook, recovery) at degrees the oracle reaches: the oracle's residual of
+    # the traces and its recovery of u from them
+    from paper_2007_11891_gb300 import HDG
+    grid = _stretched(ne, 41)
+    lam = 1.7
+    pr = Problem(ne, grid, bc, p, 25.0, lam)
+    h = HDG(ne, grid, bc, p, 25.0)
+    h.set_operator_variant("generic")
+    f = hdg_inputs.gaussian(pr.mesh.n_elem * (p + 1) ** 3, 42)
+    tr, u, info = h.solve(torch.tensor(f, device="cuda"), lam, tol=1e-10, inner=inner)
+    assert info[0]["status"] == "OK"
+    assert _oracle_residual(pr, tr.cpu().numpy(), f=f) <= 1e-10
+    u_ref, _ = pr.recover(tr.cpu().numpy(), f=f)
+    assert np.abs(u.cpu().numpy() - u_ref).max() <= 1e-9 * np.abs(u_ref).max()
+
+
+def test_degree_above_sixteen_operator_is_symmetric_positive():
+    # p = 20 (the runtime-degree kernel): K-hat symmetric and positive
+    # definite with Dirichlet sides, bitwise repeatable
+    from paper_2007_11891_gb300 import HDG
+    ne, p = (2, 1, 2), 20
+    h = HDG(ne, _stretched(ne, 43), (0, 0, 1, 1, 0, 0), p, 25.0)
+    a = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 1), device="cuda")
+    b = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 2), device="cuda")
+    ya = h.apply(a, 0.5, basis="transformed")
+    assert torch.equal(h.apply(a, 0.5, basis="transformed"), ya)
+    ab, ba = float(torch.dot(b, ya)), float(torch.dot(a, h.apply(b, 0.5, basis="transformed")))
+    assert abs(ab - ba) <= 1e-11 * max(abs(ab), 1.0)
+    assert float(torch.dot(a, ya)) > 0
