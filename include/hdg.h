@@ -212,7 +212,11 @@ hdg_status hdg_apply_static(hdg_ctx* ctx, int nrhs, const double* h_lambda, cons
  *   d_u      device, nrhs * hdg_volume_size(): recovered u, or NULL.
  *   h_info   host array of nrhs, filled on return (the call synchronises).
  * Returns the worst per-rhs status: SINGULAR (lambda = 0 without a
- * Dirichlet side), NOT_CONVERGED, BREAKDOWN, INVALID_ARG, CUDA, OOM.       */
+ * Dirichlet side), NOT_CONVERGED, BREAKDOWN, INVALID_ARG, CUDA, OOM.
+ * BREAKDOWN: an FP64 CG breakdown, a non-finite residual, or an FP32 inner
+ * breakdown after which the FP64 residual did not fall at least twofold (an
+ * FP32 inner solve that broke down after one or more iterations keeps its
+ * correction, and the refinement goes on).                                */
 hdg_status hdg_solve(hdg_ctx* ctx, int nrhs, const double* h_lambda, const double* d_f,
                      const double* d_bdry, const double* d_x0, double* d_trace, double* d_u,
                      const hdg_solve_opts* opts, hdg_solve_info* h_info, void* stream);

@@ -893,6 +893,12 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
 
   std::vector<int> active(nrhs, 1), total_it(nrhs, 0), outer(nrhs, 0), applies(nrhs, 1), status(nrhs, HDG_OK);
   std::vector<double> relres(nrhs, 0.0);
+  // a lower-precision inner solve that broke down after some iterations
+  // (loss of positive curvature in FP32 rounding, on very ill-conditioned
+  // systems) still leaves a usable correction: the refinement keeps it and
+  // goes on while the FP64 residual falls at least twofold per step
+  std::vector<int> inner_broke(nrhs, 0);
+  std::vector<double> prev_rel(nrhs, 0.0);
   bool zero_x = (x0 == nullptr);
   for (int step = 0; step <= o.max_outer; ++step) {
     // residual r-hat = F-hat - K-hat x-hat (FP64)
@@ -915,6 +921,9 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
       if (ok || !std::isfinite(relres[r])) {
         active[r] = 0;
         if (!std::isfinite(relres[r])) status[r] = HDG_ERR_BREAKDOWN;
+      } else if (inner_broke[r] && !(relres[r] <= 0.5 * prev_rel[r])) {
+        active[r] = 0;
+        status[r] = HDG_ERR_BREAKDOWN;
       } else if (step == o.max_outer || total_it[r] >= o.max_iter) {
         active[r] = 0;
         status[r] = HDG_ERR_NOT_CONVERGED;
@@ -943,7 +952,12 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
       total_it[r] += it[r];
       applies[r] += it[r];
       outer[r] += 1;
-      if (st[r] == HDG_ERR_BREAKDOWN) { status[r] = HDG_ERR_BREAKDOWN; active[r] = 0; }
+      prev_rel[r] = relres[r];
+      inner_broke[r] = 0;
+      if (st[r] == HDG_ERR_BREAKDOWN) {
+        if (o.inner == HDG_FP64 || it[r] == 0) { status[r] = HDG_ERR_BREAKDOWN; active[r] = 0; }
+        else inner_broke[r] = 1;
+      }
     }
   }
   // 6. traces in the nodal basis, u by recovery

@@ -510,9 +510,14 @@ __global__ void __launch_bounds__(tile_cta_threads(N), sizeof(T) == 4 ? (CGM ? 2
             if constexpr (i0 < N) {
               constexpr bool e0 = i0 < NE, e1 = i1 < NE, v1 = i1 < N;
               const float c0 = a.tab.c[i0], c1 = v1 ? a.tab.c[i1] : 0.f;
+              // the second lane of the last pair of an odd row (i1 = N) lies in
+              // the row padding, which no thread writes: it takes zeros, never
+              // the padding (0 x a stale NaN or Inf there would be NaN)
+              const float b0 = hh == 0 ? bv.x : bv.z, b1 = v1 ? (hh == 0 ? bv.y : bv.w) : 0.f;
+              const float k0 = hh == 0 ? cv.x : cv.z, k1 = v1 ? (hh == 0 ? cv.y : cv.w) : 0.f;
               float2 F = __fmul2_rn(make_float2(c0, c1), make_float2(e0 ? Ap : Am, e1 ? Ap : Am));
-              F = __ffma2_rn(cjd2v, hh == 0 ? make_float2(bv.x, bv.y) : make_float2(bv.z, bv.w), F);
-              F = __ffma2_rn(ckd3v, hh == 0 ? make_float2(cv.x, cv.y) : make_float2(cv.z, cv.w), F);
+              F = __ffma2_rn(cjd2v, make_float2(b0, b1), F);
+              F = __ffma2_rn(ckd3v, make_float2(k0, k1), F);
               float2 inv;
               if constexpr (DZM == 0) {
                 inv = make_float2(dzr[i0], v1 ? dzr[i1] : 0.f);
@@ -522,7 +527,7 @@ __global__ void __launch_bounds__(tile_cta_threads(N), sizeof(T) == 4 ? (CGM ? 2
                                               make_float2(dzb, dzb));
                 inv = make_float2(dz_recip(den.x), v1 ? dz_recip(den.y) : 0.f);
               } else {
-                inv = hh == 0 ? make_float2(dv.x, dv.y) : make_float2(dv.z, dv.w);
+                inv = make_float2(hh == 0 ? dv.x : dv.z, v1 ? (hh == 0 ? dv.y : dv.w) : 0.f);
               }
               const float2 u = __fmul2_rn(F, inv);
               uh[hh] = u;
