@@ -307,24 +307,34 @@ def run_ours(args, rank, world, local_rank):
         c = classes[kind]
         avg_s = c["ms"] / c["launches"] * 1e-3
         if kind == "op_fp32":
-            # the inner CG's kernel: one persistent launch per inner solve (or
-            # one launch per iteration); per CG iteration it applies the
-            # previous update and the operator
+            # the inner CG's operator kernel.  Fused step (no separate update
+            # launches): per CG iteration it applies the previous update and
+            # the operator, counted as the minimum bytes of a CG iteration.
+            # Two kernels per iteration: the operator alone, 2 T values per
+            # launch (read u, accumulate w), D_Z^-1 computed in the kernel.
+            vec = classes.get("vector", {"ms": 0.0, "launches": 0})
+            fused = vec["launches"] < fp32_iters // 2
             it_s = c["ms"] * 1e-3 / max(fp32_iters, c["launches"])
-            byts = 9.0 * T * 4
-            ach = byts / it_s / 1e9
+            pair_s = (c["ms"] + (0.0 if fused else vec["ms"])) * 1e-3 / max(fp32_iters, c["launches"])
+            min_iter_b = 9.0 * T * 4
             op_b = 2.0 * T * 4
-            return {"kernel": "tpt_tile_kernel<float> fused CG step (operator + update; persistent launch)",
-                    "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+            byts = min_iter_b if fused else op_b
+            ach = byts / it_s / 1e9
+            name = ("FP32 fused CG step (operator + update in one launch per iteration)" if fused else
+                    "tpt_fast_kernel<float> (FP32 operator of the inner CG, element runs)")
+            return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": ach / pk["hbm_gbs"], "traffic": TRAFFIC_BYTES["op_fp32"], "peak_source": "of " + src,
                     "launches_per_solve": c["launches"], "cg_iterations_per_solve": fp32_iters,
-                    "us_per_cg_iteration": it_s * 1e6, "algorithmic_bytes_per_iteration": byts,
-                    "bytes_counted": "9 T x 4 B per CG iteration, the minimum of a CG iteration (operator: read x "
-                                     "and write y, 2 T; vectors: read r, p, Ap, x and write r, p, x, 7 T); the "
-                                     "fused step moves about 12 T (it also keeps s = K p and reads the "
-                                     "preconditioner W); D_Z^-1 is computed in the kernel (0 table bytes)",
-                    "frac_operator_bytes_only": op_b / it_s / 1e9 / pk["hbm_gbs"],
-                    "frac_with_stored_dz_table": (byts + 4.0 * n ** 3 * ne_tot) / it_s / 1e9 / pk["hbm_gbs"]}
+                    "avg_launch_us": it_s * 1e6, "algorithmic_bytes_per_launch": byts,
+                    "bytes_counted": ("9 T x 4 B per CG iteration, the minimum of a CG iteration (operator: read "
+                                      "x, write y; vectors: read r, p, Ap, x, write r, p, x)" if fused else
+                                      "2 T x 4 B per launch: read the input u, write the output w (each face "
+                                      "value read by its two elements counts once); D_Z^-1 computed in the "
+                                      "kernel (0 table bytes)"),
+                    "cg_iteration": {"us": pair_s * 1e6, "min_bytes": min_iter_b,
+                                     "frac": min_iter_b / pair_s / 1e9 / pk["hbm_gbs"],
+                                     "note": "operator + update per CG iteration against the minimum bytes of "
+                                             "a CG iteration (9 T x 4 B)"}}
         if kind == "op_fp64":
             return alu(kind, "tpt_tile_kernel<double> (operator, FP64, refinement residual)",
                        (12.0 * n ** 3 + 24.0 * n ** 2) * ne_tot, avg_s,
@@ -600,8 +610,9 @@ def run_sweep(args):
 def run_probe(args):
     """Short, untimed workload for ncu captures: set-up, one warm-up, then
     `--steps` repetitions of the probed step on the chosen workload:
-      solve            mixed solve (fused CG step)
+      solve            mixed solve (CG iteration per --cg-variant)
       solve_two_kernel mixed solve with the operator + update kernel pair
+      solve_fp64       solve with the FP64 inner CG
       apply32/64/bf16  one transformed-basis operator application
       nodal_fused      one nodal FP64 apply by the one-kernel HDG-TP operator
       lowdim2          one 2D operator application (512 x 512 elements, p = 8)
@@ -612,6 +623,8 @@ def run_probe(args):
     torch.cuda.set_device(0)
     cfg = hdg_inputs.WORKLOADS[args.workload]
     ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"] or 1.0
+    if args.degree:
+        p = args.degree
     if args.probe == "lowdim2":
         ne2 = (512, 512)
         h = HDGLowDim(ne2, [np.linspace(0.0, 1.0, v + 1) for v in ne2], (0,) * 4, 8, hdg_inputs.TAU_HAT)
@@ -620,13 +633,16 @@ def run_probe(args):
         step = lambda: h.apply(x, 1.0, basis="transformed", out=y)
     else:
         h = HDG(ne, hdg_inputs.grid_lines(ne, cfg["stretched"]), (0,) * 6, p, hdg_inputs.TAU_HAT)
+        h.set_operator_variant(args.op_variant)
+        h.set_cg_variant(args.cg_variant)
         if args.eager:
             h.profile(True)   # per-launch events; keeps the solver off CUDA graphs
-        if args.probe in ("solve", "solve_two_kernel"):
+        if args.probe in ("solve", "solve_two_kernel", "solve_fp64"):
             if args.probe == "solve_two_kernel":
                 h.set_cg_variant("two_kernel")
             f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11890), device="cuda")
-            step = lambda: h.solve(f, lam, tol=1e-10, inner="fp32", return_u=True)
+            inner = "fp64" if args.probe == "solve_fp64" else "fp32"
+            step = lambda: h.solve(f, lam, tol=1e-10, inner=inner, return_u=True)
         elif args.probe == "nodal_fused":
             h.set_nodal_variant("fused")
             x = torch.tensor(hdg_inputs.uniform_pm1(h.trace_size, 11893), device="cuda")
@@ -654,8 +670,13 @@ def main():
     ap.add_argument("--sweep", action="store_true", help="extra measurements instead of the bench line")
     ap.add_argument("--parts", default="operator,nodal,lowdim,paper,bf16,adjoint,batched",
                     help="sweep sections to run (comma-separated)")
-    ap.add_argument("--probe", choices=["solve", "solve_two_kernel", "apply32", "apply64", "apply_bf16",
-                                        "nodal_fused", "lowdim2"], help="untimed workload for ncu")
+    ap.add_argument("--probe", choices=["solve", "solve_two_kernel", "solve_fp64", "apply32", "apply64",
+                                        "apply_bf16", "nodal_fused", "lowdim2"], help="untimed workload for ncu")
+    ap.add_argument("--op-variant", default="auto", choices=["auto", "runs", "tiles", "generic"],
+                    help="probe: operator kernel (hdg_set_operator_variant)")
+    ap.add_argument("--cg-variant", default="auto", choices=["auto", "persistent", "fused", "two_kernel"],
+                    help="probe: inner CG iteration (hdg_set_cg_variant)")
+    ap.add_argument("--degree", type=int, default=0, help="probe: polynomial degree instead of the workload's")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(hdg_inputs.WORKLOADS))
     ap.add_argument("--eager", action="store_true",
                     help="probe: launch the CG loop kernel by kernel (no CUDA graphs), so that profilers that "

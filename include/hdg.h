@@ -274,7 +274,8 @@ hdg_status hdg_autotune(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_prec
 hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
 
 /* Tuning (not part of the method): work split of the operator kernel.
- * 0 automatic (element tiles); 2 element tiles (CTAs of n^2 G threads take
+ * 0 automatic (element tiles for FP64 arithmetic and BF16 storage, element
+ * runs for FP32: the choice that measured fastest); 2 element tiles (CTAs of n^2 G threads take
  * tiles of consecutive elements in element order, one face node / x1-line
  * per thread; hdg_set_x1_segment sets the elements per tile, rounded to a
  * multiple of G); 1 element runs (one thread per x1-line, runs of elements
@@ -288,8 +289,10 @@ hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
 hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant);
 
 /* Tuning (not part of the method): how an inner CG iteration runs.
- *   0 (default) with the element-tile operator kernel
- *     (hdg_set_operator_variant 0 or 2): the whole inner CG in one
+ *   3 (default) as 1, two kernels per iteration (measured fastest on the
+ *     meshes of 8^3 to 32^3 elements tried, in FP32 and FP64);
+ *   0 with the element-tile operator kernel (hdg_set_operator_variant 0
+ *     or 2; the fused step always uses the tile kernel): the whole inner CG in one
  *     cooperative launch of that kernel (every CTA resident; per iteration,
  *     each CTA applies the CG update of the previous iteration to every face
  *     value it reads -- each face value's one owner stores the new x, p, r,
@@ -303,7 +306,7 @@ hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant);
  * All compute the same CG iterates in exact arithmetic.  A grid barrier that
  * waits too long (CTAs not co-resident) ends the kernel and the solve
  * returns HDG_ERR_CUDA.  Errors: INVALID_ARG (NULL context, variant outside
- * 0..2).                                                                  */
+ * 0..3).                                                                  */
 hdg_status hdg_set_cg_variant(hdg_ctx* ctx, int variant);
 
 /* Which kernel applies K in the nodal basis (hdg_apply with HDG_FP64 and

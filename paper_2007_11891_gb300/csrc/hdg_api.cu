@@ -105,12 +105,12 @@ struct hdg_ctx {
   DevBuf loopctl;   // device loop-trip counter of the CG loop graph
   int seg_override = 0;   // x1 segment length; 0 = automatic
   int ppb_override = 0;   // slots per CTA; 0 = automatic
-  int op_variant = 0;     // apply kernel: 0 automatic (tiles), 1 element runs, 2 element tiles, 3 runtime degree
+  int op_variant = 0;     // apply kernel: 0 automatic (use_tiles), 1 element runs, 2 element tiles, 3 runtime degree
   int nodal_variant = 0;  // FP64 nodal apply: 0 face-wise transforms + transformed kernel, 1 one kernel (HDG-TP)
   int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
   int fused_cg = 0;       // the current inner CG runs the fused tile-kernel step
-  int fused_enabled = 1;  // allow the fused step (hdg_set_cg_variant)
-  int persist_enabled = 1;  // run the fused step as one persistent cooperative launch
+  int fused_enabled = 0;  // allow the fused step (hdg_set_cg_variant)
+  int persist_enabled = 0;  // run the fused step as one persistent cooperative launch
 };
 
 namespace {
@@ -237,6 +237,17 @@ hdg_status ensure_dinv(hdg_ctx* c, int nrhs, const double* lam, cudaStream_t s, 
   return HDG_OK;
 }
 
+// Whether the apply of arithmetic T / storage ST runs the element-tile
+// kernel.  Automatic choice, from solve and apply timings on this part: the
+// tiles for FP64 arithmetic and BF16 storage, the element runs for FP32
+// (shorter per-element latency; equal or faster on every measured mesh).
+template <typename T, typename ST>
+bool use_tiles(const hdg_ctx* c) {
+  if (c->op_variant == 1 || c->op_variant == 3) return false;
+  if (c->op_variant == 2) return true;
+  return sizeof(T) == 8 || sizeof(ST) == 2;
+}
+
 template <typename T, typename ST>
 hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mode = hdg::TPT_APPLY) {
   hdg::TptArgs<T, ST> a{};
@@ -261,9 +272,8 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mod
   a.max_grid = ctas;
   a.sms = c->sms;
   a.tile = c->seg_override;   // elements per tile of the tile kernel (0 = automatic)
-  // apply kernel: element tiles (tpt_tile.cuh) unless another work split is
-  // asked for; the FP64 and BF16 applies have the tiles and the element runs
-  if (mode == hdg::TPT_APPLY && c->op_variant != 1) a.variant = 3;
+  // apply kernel: element tiles (tpt_tile.cuh) or element runs (use_tiles)
+  if (mode == hdg::TPT_APPLY && use_tiles<T, ST>(c)) a.variant = 3;
   if (c->op_variant == 3) a.variant = 4;   // runtime-degree kernel, every mode
   // FP32 apply: equal contiguous runs, one per slot of a resident wave (per
   // right-hand side: the wave is shared by the batch)
@@ -364,7 +374,7 @@ hdg_status ensure_reductions(hdg_ctx* c, int nrhs) {
   if (fresh) HDG_CUDA(cudaMemset(c->counters.p, 0, c->counters.bytes));
   HDG_TRY(ensure(c->cgs, sizeof(hdg::CgScalars) * (size_t)nrhs));
   HDG_TRY(ensure(c->flags, sizeof(int) * (size_t)nrhs));
-  HDG_TRY(ensure(c->scal, sizeof(double) * (size_t)nrhs * 4));   // rz0, pq, tol, spare
+  HDG_TRY(ensure(c->scal, sizeof(double) * (size_t)nrhs * 4));   // rz0, pq, tol, FP32 inner-solve scale
   return HDG_OK;
 }
 
@@ -724,12 +734,13 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
 template <typename T>
 hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat, const std::vector<double>& tol_r,
                     const std::vector<int>& active, const std::vector<int>& max_it, bool use_pc,
-                    std::vector<int>& iters, std::vector<int>& status, cudaStream_t s) {
+                    std::vector<int>& iters, std::vector<int>& status, cudaStream_t s,
+                    const double* scale = nullptr) {
   const long long T_ = c->ntrace;
   const long long tot = T_ * nrhs;
-  // the fused step (one tile-kernel launch per iteration) whenever the tile
-  // kernel is the operator; the two-kernel loop (operator, cg_step_kernel)
-  // for the other work splits
+  // the fused step (a mode of the tile kernel) where hdg_set_cg_variant asks
+  // for it and the tile kernel can run; else the two-kernel loop (operator,
+  // cg_step_kernel)
   c->fused_cg = (c->fused_enabled && (c->op_variant == 0 || c->op_variant == 2) && c->n <= hdg::kMaxSpecialisedN) ? 1 : 0;
   for (int i : {W_R, W_D, W_P, W_Q, W_U, W_S}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
   if (c->fused_cg) {
@@ -753,6 +764,7 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   hdg::CgScalars* cg = static_cast<hdg::CgScalars*>(c->cgs.p);
 
   if (sizeof(T) == 8) HDG_CUDA(cudaMemcpyAsync(r, rhat, sizeof(double) * tot, cudaMemcpyDeviceToDevice, s));
+  else if (scale) { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_scale_convert(rhat, reinterpret_cast<float*>(r), T_, nrhs, scale, s)); }
   else { Timed t_(c, K_VEC, s); HDG_CUDA((hdg::launch_convert<double, float>(rhat, reinterpret_cast<float*>(r), tot, s))); }
   for (T* v : {d, p, q, u, wsp<T>(c, W_S)}) HDG_CUDA(cudaMemsetAsync(v, 0, sizeof(T) * tot, s));
   if (c->fused_cg)
@@ -943,8 +955,18 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
       HDG_TRY(inner_cg<double>(c, nrhs, lam, rhat, tol_r, active, caps, o.precond != 0, it, st, s));
       { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_to<double>(xhat, wsp<double>(c, W_D), tot, s)); }
     } else {
-      HDG_TRY(inner_cg<float>(c, nrhs, lam, rhat, tol_r, active, caps, o.precond != 0, it, st, s));
-      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_to<float>(xhat, wsp<float>(c, W_D), tot, s)); }
+      // the FP32 system is scaled per rhs by a power of two that brings the
+      // residual norm near 1 (residuals of large data would overflow the
+      // FP32 inner products); the correction is scaled back exactly
+      std::vector<double> sc(nrhs, 1.0);
+      for (int r = 0; r < nrhs; ++r) {
+        const double nr = std::sqrt(normR2[r]);
+        if (nr > 0.0 && std::isfinite(nr)) sc[r] = std::ldexp(1.0, -std::ilogb(nr));
+      }
+      double* sc_dev = static_cast<double*>(c->scal.p) + 3 * nrhs;
+      HDG_CUDA(cudaMemcpyAsync(sc_dev, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+      HDG_TRY(inner_cg<float>(c, nrhs, lam, rhat, tol_r, active, caps, o.precond != 0, it, st, s, sc_dev));
+      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_unscaled(xhat, wsp<float>(c, W_D), T_, nrhs, sc_dev, s)); }
     }
     zero_x = false;
     for (int r = 0; r < nrhs; ++r) {
@@ -1067,7 +1089,7 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
   HDG_CUDA(cudaMemsetAsync(c->ws[W_XHAT].p, 0x3c, esz * tot, s));   // finite, non-zero pattern
   // candidate segment lengths (distinct splits of the x1-pencils) and slots;
   // for the tile kernel: elements per tile, no slots
-  const bool tiles = c->op_variant == 0 || c->op_variant == 2;
+  const bool tiles = prec == HDG_FP64 ? use_tiles<double, double>(c) : use_tiles<float, float>(c);
   std::vector<int> segs = {0};
   if (tiles) {
     for (int e : {2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32}) segs.push_back(e);
@@ -1146,8 +1168,8 @@ hdg_status hdg_set_operator_variant(hdg_ctx* c, int variant) {
 }
 
 hdg_status hdg_set_cg_variant(hdg_ctx* c, int variant) {
-  if (!c || variant < 0 || variant > 2) return fail(HDG_ERR_INVALID_ARG, "NULL context or CG variant outside 0..2");
-  c->fused_enabled = variant != 1 ? 1 : 0;
+  if (!c || variant < 0 || variant > 3) return fail(HDG_ERR_INVALID_ARG, "NULL context or CG variant outside 0..3");
+  c->fused_enabled = (variant == 0 || variant == 2) ? 1 : 0;
   c->persist_enabled = variant == 0 ? 1 : 0;
   return HDG_OK;
 }

@@ -103,6 +103,12 @@ cudaError_t launch_convert(const TI* x, TO* y, long long count, cudaStream_t s);
 cudaError_t launch_sub(const double* a, const double* b, double* out, long long count, cudaStream_t s);  // out = a - b
 template <typename T>
 cudaError_t launch_add_to(double* x, const T* d, long long count, cudaStream_t s);  // x += d
+// per right-hand side r (vectors of length len): y[r] = (float)(scale[r] x[r]),
+// and x[r] += d[r] / scale[r]; scale (device, nrhs) holds powers of two
+cudaError_t launch_scale_convert(const double* x, float* y, long long len, int nrhs, const double* scale,
+                                 cudaStream_t s);
+cudaError_t launch_add_unscaled(double* x, const float* d, long long len, int nrhs, const double* scale,
+                                cudaStream_t s);
 
 // deterministic dot products sum_i a_i b_i (w_i) per right-hand side into
 // out[r]; w may be null (partials[nrhs * blocks], counter[nrhs] zero on

@@ -423,6 +423,25 @@ __global__ void add_to_kernel(double* __restrict__ x, const T* __restrict__ d, l
     x[t] += static_cast<double>(d[t]);
 }
 
+// y[r] = scale[r] x[r] in FP32 (grid.y = rhs); scale[r] is a power of two,
+// so the scaling itself is exact and only the conversion rounds
+__global__ void scale_convert_kernel(const double* __restrict__ x, float* __restrict__ y, long long len,
+                                     const double* __restrict__ scale) {
+  const long long o = (long long)blockIdx.y * len;
+  const double sc = scale[blockIdx.y];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x)
+    y[o + t] = static_cast<float>(sc * x[o + t]);
+}
+
+// x[r] += d[r] / scale[r] (exact division by a power of two)
+__global__ void add_unscaled_kernel(double* __restrict__ x, const float* __restrict__ d, long long len,
+                                    const double* __restrict__ scale) {
+  const long long o = (long long)blockIdx.y * len;
+  const double inv = 1.0 / scale[blockIdx.y];
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x)
+    x[o + t] += inv * static_cast<double>(d[o + t]);
+}
+
 // block sum of a double, result valid in thread 0
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double ws[32];
@@ -836,6 +855,22 @@ template cudaError_t launch_convert<float, double>(const float*, double*, long l
 template cudaError_t launch_convert<double, double>(const double*, double*, long long, cudaStream_t);
 template cudaError_t launch_convert<double, __nv_bfloat16>(const double*, __nv_bfloat16*, long long,
                                                           cudaStream_t);
+
+cudaError_t launch_scale_convert(const double* x, float* y, long long len, int nrhs, const double* scale,
+                                 cudaStream_t s) {
+  if (len <= 0 || nrhs <= 0) return cudaSuccess;
+  dim3 grid(grid_for(len, kVecThreads), nrhs);
+  scale_convert_kernel<<<grid, kVecThreads, 0, s>>>(x, y, len, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_unscaled(double* x, const float* d, long long len, int nrhs, const double* scale,
+                                cudaStream_t s) {
+  if (len <= 0 || nrhs <= 0) return cudaSuccess;
+  dim3 grid(grid_for(len, kVecThreads), nrhs);
+  add_unscaled_kernel<<<grid, kVecThreads, 0, s>>>(x, d, len, scale);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sub(const double* a, const double* b, double* out, long long count, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;

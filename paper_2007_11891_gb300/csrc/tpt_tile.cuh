@@ -45,10 +45,15 @@
 
 namespace hdg {
 
-// Shared-memory footprint of the tile kernel, in elements of T, for tile
-// size E (rows of R = dz_row(N) entries, padded for 16-byte reads).
+// Row length R of the tile kernel's shared-memory rows (SD2, SD3, U): the
+// D_Z^-1 table row dz_row(N), padded for 16-byte reads, and for FP32 rows of
+// more than 8 entries a multiple of 8 plus 4, so that the 16-byte row
+// accesses of 8 consecutive threads (one shared-memory wavefront) fall in
+// distinct banks (rows of 16 words put two of them on the same banks).
 template <typename T, int N>
-__host__ __device__ constexpr int tile_row() { return dz_row(N, sizeof(T)); }
+__host__ __device__ constexpr int tile_row() {
+  return (sizeof(T) == 4 && N > 8 && dz_row(N, 4) % 8 == 0) ? dz_row(N, 4) + 4 : dz_row(N, sizeof(T));
+}
 template <typename T, int N>
 __host__ __device__ constexpr int tile_smem_per_elem() {
   // SD2, SD3 (2 x N rows each), U (N^2 rows), X1, X1H, OX1 (lo, hi): N^2 each
@@ -260,7 +265,7 @@ __global__ void __launch_bounds__(tile_cta_threads(N), sizeof(T) == 4 ? (CGM ? 2
   constexpr bool DZC = DZM == 1;
   constexpr int N2 = N * N, NE = (N + 1) / 2;
   constexpr int R = tile_row<T, N>();
-  constexpr int VL = Vec<T>::L, NQ = R / VL;
+  constexpr int VL = Vec<T>::L, NQ = (N + VL - 1) / VL;   // vectors covering a row (R may pad further)
   using V = typename Vec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -341,12 +346,14 @@ __global__ void __launch_bounds__(tile_cta_threads(N), sizeof(T) == 4 ? (CGM ? 2
   const T lj = a.tab.lam[qa], lk = a.tab.lam[qb];
   const int rowB = (qa < NE ? 0 : N * R) + R * qb;   // (S2|D2)(., k) by the parity of j
   const int rowC = (qb < NE ? 0 : N * R) + R * qa;   // (S3|D3)(., j) by the parity of k
-  const int line = R * (qa + N * qb);                // U row (j, k); D_Z^-1 row (j, k)
+  constexpr int RT = dz_row(N, sizeof(T));          // D_Z^-1 table row
+  const int line = R * (qa + N * qb);                // U row (j, k)
+  const int dzline = RT * (qa + N * qb);             // D_Z^-1 row (j, k)
   const int node = R * qb + qa;                      // face node (a, b) in a row array
   // uniform grid: the thread's row of the D_Z^-1 table in registers
   T dzr[N];
   if constexpr (DZM == 0) {
-    const T* dz = a.dinv + (long long)rhs * a.dinv_rhs_stride + line;
+    const T* dz = a.dinv + (long long)rhs * a.dinv_rhs_stride + dzline;
     static_for<0, N>([&](auto ic) { dzr[decltype(ic)::value] = dz[decltype(ic)::value]; });
   }
 
@@ -485,7 +492,7 @@ __global__ void __launch_bounds__(tile_cta_threads(N), sizeof(T) == 4 ? (CGM ? 2
       const T* Bs = SD2 + el * 2 * N * R + rowB;
       const T* Cs = SD3 + el * 2 * N * R + rowC;
       const T* dzg = nullptr;
-      if constexpr (DZM == 2) dzg = a.dinv + (long long)rhs * a.dinv_rhs_stride + (long long)o.elem * (N2 * R) + line;
+      if constexpr (DZM == 2) dzg = a.dinv + (long long)rhs * a.dinv_rhs_stride + (long long)o.elem * (N2 * RT) + dzline;
       T dzb = T(0);
       if constexpr (DZC) dzb = fma(d3, lk, fma(d2, lj, lam_r * d0));
       T* Ur = U + el * N2 * R + line;

@@ -111,18 +111,19 @@ class HDG:
         _capi.check(_capi.lib().hdg_set_dz_mode(self._h, code), "hdg_set_dz_mode")
 
     def set_operator_variant(self, variant):
-        """Operator kernel: 'auto' or 'tiles' (element tiles), 'runs' (one
-        thread per x1-line in element runs) or 'generic' (the runtime-degree
-        kernel that degrees above 16 use, any degree)."""
+        """Operator kernel: 'auto' (tiles for FP64 and BF16 storage, runs for
+        FP32), 'tiles' (element tiles), 'runs' (one thread per x1-line in
+        element runs) or 'generic' (the runtime-degree kernel that degrees
+        above 16 use, any degree)."""
         code = {"auto": 0, "runs": 1, "tiles": 2, "generic": 3}[variant]
         _capi.check(_capi.lib().hdg_set_operator_variant(self._h, code), "hdg_set_operator_variant")
 
     def set_cg_variant(self, variant):
-        """Inner CG iteration: 'persistent' (the default with the tile
-        operator: the whole inner CG in one cooperative launch), 'fused' (one
-        tile-kernel launch per iteration) or 'two_kernel' (operator, then the
-        vector update)."""
-        code = {"persistent": 0, "fused": 2, "two_kernel": 1}[variant]
+        """Inner CG iteration: 'auto' (the default: two kernels), 'persistent'
+        (the whole inner CG in one cooperative launch of the tile kernel),
+        'fused' (one tile-kernel launch per iteration) or 'two_kernel'
+        (operator, then the vector update)."""
+        code = {"persistent": 0, "fused": 2, "two_kernel": 1, "auto": 3}[variant]
         _capi.check(_capi.lib().hdg_set_cg_variant(self._h, code), "hdg_set_cg_variant")
 
     def set_nodal_variant(self, variant):
