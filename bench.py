@@ -348,12 +348,12 @@ def run_ours(args, rank, world, local_rank):
         if kind == "rhs_recover":
             return alu(kind, "tpt_kernel<double> RHS / RECOVER modes", (13.0 * n ** 3 + 24.0 * n ** 2) * ne_tot,
                        avg_s, "executed: 13 n^3 + 24 n^2 per element")
-        byts = 13.0 * T * 4
+        byts = 12.0 * T * 4
         ach = byts / avg_s / 1e9
         return {"kernel": "CG vector kernels (cg_step_kernel<float> and the solve's other vector launches)",
                 "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
                 "traffic": None, "peak_source": "of " + src, "avg_launch_us": avg_s * 1e6,
-                "bytes_counted": "13 streams of T FP32 values per launch (cg_step_kernel reads u, w, p, s, x, r, W "
+                "bytes_counted": "12 streams of T FP32 values per launch (cg_step_kernel reads w, p, s, x, r, W "
                                  "and writes p, s, x, r, u, w); the average includes the few other vector launches"}
 
     roofline = roof(dominant)

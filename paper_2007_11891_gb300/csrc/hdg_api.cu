@@ -374,7 +374,7 @@ hdg_status ensure_reductions(hdg_ctx* c, int nrhs) {
   if (fresh) HDG_CUDA(cudaMemset(c->counters.p, 0, c->counters.bytes));
   HDG_TRY(ensure(c->cgs, sizeof(hdg::CgScalars) * (size_t)nrhs));
   HDG_TRY(ensure(c->flags, sizeof(int) * (size_t)nrhs));
-  HDG_TRY(ensure(c->scal, sizeof(double) * (size_t)nrhs * 4));   // rz0, pq, tol, FP32 inner-solve scale
+  HDG_TRY(ensure(c->scal, sizeof(double) * (size_t)nrhs * 5));   // rz0, pq, tol, FP32 inner-solve scale and inverse
   return HDG_OK;
 }
 
@@ -453,7 +453,16 @@ hdg_status cg_fused_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* Wt,
   T* S[2] = {wsp<T>(c, W_S), wsp<T>(c, W_S2)};
   T* Wb[3] = {wsp<T>(c, W_Q), wsp<T>(c, W_W2), wsp<T>(c, W_W3)};
   hdg::TptArgs<T, T> a = base_args<T, T>(c, dinv, nrhs);
-  a.variant = 3;
+  if (sizeof(T) == 4 && !use_tiles<T, T>(c)) {
+    // the element-run kernel: runs sized for its own occupancy with the
+    // staging areas of the fused step
+    a.variant = 0;
+    const long long slots = std::max(1LL, (long long)c->sms * hdg::fast_fused_blocks_per_sm(c->n, a.ppb) * a.ppb);
+    const long long nel = (long long)c->nelem * std::max(nrhs, 1);
+    a.chunk = c->seg_override > 0 ? c->seg_override : (int)std::max(1LL, (nel + slots - 1) / slots);
+  } else {
+    a.variant = 3;
+  }
   a.cg = 1;
   a.skip = flags;
   a.hook = hook;
@@ -591,7 +600,7 @@ bool cg_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p,
                                 (uintptr_t)c->cgs.p, (uintptr_t)c->scal.p, (uintptr_t)c->partials.p,
                                 (uintptr_t)c->step_partials.p, (uintptr_t)c->counters.p, (uintptr_t)count,
                                 (uintptr_t)c->pdl, (uintptr_t)c->seg_override,
-                                (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode, (uintptr_t)c->fused_cg,
+                                (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode, (uintptr_t)c->fused_cg, (uintptr_t)c->op_variant,
                                 (uintptr_t)c->ws[W_R2].p, (uintptr_t)c->ws[W_S2].p, (uintptr_t)c->ws[W_W2].p,
                                 (uintptr_t)c->ws[W_W3].p, (uintptr_t)c->ws[W_GP].p};
   GraphEntry* ge = nullptr;
@@ -654,7 +663,7 @@ bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, 
                                 (uintptr_t)c->partials.p, (uintptr_t)c->step_partials.p,
                                 (uintptr_t)c->counters.p, (uintptr_t)c->loopctl.p,
                                 (uintptr_t)c->seg_override, (uintptr_t)c->ppb_override, (uintptr_t)c->dz_mode,
-                                (uintptr_t)c->pdl, (uintptr_t)c->fused_cg, (uintptr_t)c->ws[W_R2].p,
+                                (uintptr_t)c->pdl, (uintptr_t)c->fused_cg, (uintptr_t)c->op_variant, (uintptr_t)c->ws[W_R2].p,
                                 (uintptr_t)c->ws[W_S2].p, (uintptr_t)c->ws[W_W2].p, (uintptr_t)c->ws[W_W3].p,
                                 (uintptr_t)c->ws[W_GP].p};
   GraphEntry* ge = nullptr;
@@ -741,7 +750,9 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
   // the fused step (a mode of the tile kernel) where hdg_set_cg_variant asks
   // for it and the tile kernel can run; else the two-kernel loop (operator,
   // cg_step_kernel)
-  c->fused_cg = (c->fused_enabled && (c->op_variant == 0 || c->op_variant == 2) && c->n <= hdg::kMaxSpecialisedN) ? 1 : 0;
+  // (FP32: element runs or tiles; FP64: tiles only)
+  c->fused_cg = (c->fused_enabled && c->op_variant != 3 && c->n <= hdg::kMaxSpecialisedN &&
+                 !(sizeof(T) == 8 && c->op_variant == 1)) ? 1 : 0;
   for (int i : {W_R, W_D, W_P, W_Q, W_U, W_S}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
   if (c->fused_cg) {
     for (int i : {W_R2, W_S2, W_W2, W_W3}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
@@ -958,15 +969,19 @@ hdg_status solve_impl(hdg_ctx* c, int nrhs, const double* lam, const double* vol
       // the FP32 system is scaled per rhs by a power of two that brings the
       // residual norm near 1 (residuals of large data would overflow the
       // FP32 inner products); the correction is scaled back exactly
-      std::vector<double> sc(nrhs, 1.0);
+      std::vector<double> sc(2 * (size_t)nrhs, 1.0);   // scales, then their inverses
       for (int r = 0; r < nrhs; ++r) {
         const double nr = std::sqrt(normR2[r]);
-        if (nr > 0.0 && std::isfinite(nr)) sc[r] = std::ldexp(1.0, -std::ilogb(nr));
+        if (nr > 0.0 && std::isfinite(nr)) {
+          const int e = std::ilogb(nr);
+          sc[r] = std::ldexp(1.0, -e);
+          sc[nrhs + r] = std::ldexp(1.0, e);
+        }
       }
       double* sc_dev = static_cast<double*>(c->scal.p) + 3 * nrhs;
-      HDG_CUDA(cudaMemcpyAsync(sc_dev, sc.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+      HDG_CUDA(cudaMemcpyAsync(sc_dev, sc.data(), sizeof(double) * 2 * nrhs, cudaMemcpyHostToDevice, s));
       HDG_TRY(inner_cg<float>(c, nrhs, lam, rhat, tol_r, active, caps, o.precond != 0, it, st, s, sc_dev));
-      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_unscaled(xhat, wsp<float>(c, W_D), T_, nrhs, sc_dev, s)); }
+      { Timed t_(c, K_VEC, s); HDG_CUDA(hdg::launch_add_unscaled(xhat, wsp<float>(c, W_D), T_, nrhs, sc_dev + nrhs, s)); }
     }
     zero_x = false;
     for (int r = 0; r < nrhs; ++r) {

@@ -26,6 +26,8 @@ void tpt_split(int n, const int ne[3], int nrhs, int ctas, int ppb, int* seg, in
 // resident CTAs per SM of tpt_kernel<T, ST, n, mode> at ppb slots per CTA
 template <typename T, typename ST>
 int tpt_blocks_per_sm(int mode, int n, int ppb);
+// CTAs per SM of the FP32 element-run kernel with the fused CG step
+int fast_fused_blocks_per_sm(int n, int ppb);
 // any mode for degrees above the specialised kernels (tpt_generic.cuh):
 // D_Z^-1 computed in the kernel, a.dinv ignored
 template <typename T>
@@ -104,10 +106,11 @@ cudaError_t launch_sub(const double* a, const double* b, double* out, long long 
 template <typename T>
 cudaError_t launch_add_to(double* x, const T* d, long long count, cudaStream_t s);  // x += d
 // per right-hand side r (vectors of length len): y[r] = (float)(scale[r] x[r]),
-// and x[r] += d[r] / scale[r]; scale (device, nrhs) holds powers of two
+// and x[r] += inv_scale[r] d[r]; scale, inv_scale (device, nrhs) hold powers
+// of two
 cudaError_t launch_scale_convert(const double* x, float* y, long long len, int nrhs, const double* scale,
                                  cudaStream_t s);
-cudaError_t launch_add_unscaled(double* x, const float* d, long long len, int nrhs, const double* scale,
+cudaError_t launch_add_unscaled(double* x, const float* d, long long len, int nrhs, const double* inv_scale,
                                 cudaStream_t s);
 
 // deterministic dot products sum_i a_i b_i (w_i) per right-hand side into

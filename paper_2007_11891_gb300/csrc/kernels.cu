@@ -433,11 +433,11 @@ __global__ void scale_convert_kernel(const double* __restrict__ x, float* __rest
     y[o + t] = static_cast<float>(sc * x[o + t]);
 }
 
-// x[r] += d[r] / scale[r] (exact division by a power of two)
+// x[r] += inv_scale[r] d[r] (inv_scale a power of two: exact)
 __global__ void add_unscaled_kernel(double* __restrict__ x, const float* __restrict__ d, long long len,
-                                    const double* __restrict__ scale) {
+                                    const double* __restrict__ inv_scale) {
   const long long o = (long long)blockIdx.y * len;
-  const double inv = 1.0 / scale[blockIdx.y];
+  const double inv = inv_scale[blockIdx.y];
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < len; t += (long long)gridDim.x * blockDim.x)
     x[o + t] += inv * static_cast<double>(d[o + t]);
 }
@@ -576,7 +576,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nvec = (len % 4 == 0) ? len / 4 : 0;
-  // The first group's u, p, s, x, r and W were written by the update launch
+  // u_i = W r_i is formed again from W and r (bitwise the stored product)
+  // instead of being read: 6 streams read (w, p, s, x, r, W), 6 written.
+  // The first group's p, s, x, r and W were written by the update launch
   // before the operator (complete before the operator's blocks passed their
   // own wait, hence before this launch began), and the operator does not
   // write them: they are loaded while the operator's last block is still
@@ -585,7 +587,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
   T uv[4], wq[4], pv[4], sq[4], xv[4], rv[4], mv[4] = {T(1), T(1), T(1), T(1)};
   if (tid < nvec) {
     const long long t = o + 4 * tid;
-    ld4(u + t, uv);
     ld4(p + t, pv);
     ld4(sv + t, sq);
     ld4(x + t, xv);
@@ -600,7 +601,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
   for (long long v = tid; v < nvec; v += stride) {
     const long long t = o + 4 * v;
     if (v != tid) {
-      ld4(u + t, uv);
       ld4(p + t, pv);
       ld4(sv + t, sq);
       ld4(x + t, xv);
@@ -611,7 +611,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
     const T al = static_cast<T>(cg[r].alpha), be = static_cast<T>(cg[r].beta);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      pv[k] = fma(be, pv[k], uv[k]);
+      pv[k] = fma(be, pv[k], mv[k] * rv[k]);   // u = W r of this iteration, bitwise as stored
       sq[k] = fma(be, sq[k], wq[k]);
       xv[k] = fma(al, pv[k], xv[k]);
       rv[k] = fma(-al, sq[k], rv[k]);
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
   {
     const T al = static_cast<T>(cg[r].alpha), be = static_cast<T>(cg[r].beta);
     for (long long t = o + nvec * 4 + tid; t < o + len; t += stride) {
-      const T pn = fma(be, p[t], u[t]);
+      const T pn = fma(be, p[t], (W ? W[t] : T(1)) * rvec[t]);
       const T sn = fma(be, sv[t], wv[t]);
       const T rn = fma(-al, sn, rvec[t]);
       const T un = (W ? W[t] : T(1)) * rn;
@@ -864,11 +864,11 @@ cudaError_t launch_scale_convert(const double* x, float* y, long long len, int n
   return cudaGetLastError();
 }
 
-cudaError_t launch_add_unscaled(double* x, const float* d, long long len, int nrhs, const double* scale,
+cudaError_t launch_add_unscaled(double* x, const float* d, long long len, int nrhs, const double* inv_scale,
                                 cudaStream_t s) {
   if (len <= 0 || nrhs <= 0) return cudaSuccess;
   dim3 grid(grid_for(len, kVecThreads), nrhs);
-  add_unscaled_kernel<<<grid, kVecThreads, 0, s>>>(x, d, len, scale);
+  add_unscaled_kernel<<<grid, kVecThreads, 0, s>>>(x, d, len, inv_scale);
   return cudaGetLastError();
 }
 

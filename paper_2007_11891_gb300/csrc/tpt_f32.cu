@@ -20,6 +20,15 @@ int tpt_blocks_per_sm<float, float>(int mode, int n, int ppb) {
   return tpt_occupancy_dispatch<float, float>(mode, n, ppb);
 }
 
+// CTAs per SM of the element-run kernel with the fused CG step (its
+// staging areas take extra shared memory); the lower of the two D_Z^-1 forms
+int fast_fused_blocks_per_sm(int n, int ppb) {
+#define OCC(N) std::min(fast_occupancy<N, false, 1>(ppb), fast_occupancy<N, true, 1>(ppb))
+  FAST_N_SWITCH(n, OCC)
+#undef OCC
+  return 1;
+}
+
 template <>
 cudaError_t launch_tpt<float, float>(int mode, int n, TptArgs<float, float> a, int nrhs, cudaStream_t s) {
   if (n > kMaxSpecialisedN || a.variant == 4) return launch_generic<float>(mode, n, a, nrhs, s);

@@ -23,7 +23,7 @@
 // that, here too, each face value is the same two-term sum whatever the runs).
 #pragma once
 
-#include "tpt_kernel.cuh"
+#include "cg_fused.cuh"
 
 namespace hdg {
 
@@ -33,9 +33,22 @@ struct FaceOffsets {
   int x1l, x1h, x2l, x2h, x3l, x3h;
 };
 
-template <int N, bool DZC, typename ST = float>
+// Fused CG step (CGM = 1, FP32 storage only): the launch of iteration
+// i + 1 stages, for every face value it reads, r, w = K u, s = K p and W of
+// iteration i (and p, x at the face's owner: the element below it, or its
+// only element) with asynchronous copies into this thread's part of shared
+// memory while the previous element computes; it then forms
+//   s' = w + beta s,  r' = r - alpha s',  u' = W r'
+// and applies the operator to u'.  The owner also stores p' = W r + beta p,
+// x' = x + alpha p', s', r', a zero into the w buffer of the launch after
+// next, and adds r' . u' to gamma (CgVecs; alpha, beta from the previous
+// launch's last block).  Each face value is updated by exactly the same
+// arithmetic wherever it is read, so both readers see the same u'.
+template <int N, bool DZC, typename ST = float, int CGM = 0>
 __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
     tpt_fast_kernel(const TptArgs<float, ST> a) {
+  constexpr bool CG = CGM != 0;
+  static_assert(!CG || std::is_same<ST, float>::value, "the fused CG step runs on FP32 storage");
   // FP32 storage sums the x1-face between consecutive elements of a run in
   // registers; BF16 storage adds both contributions atomically (a register
   // sum would round once where the atomics round twice)
@@ -54,6 +67,12 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   if (a.skip && a.skip[rhs]) return;   // uniform per block
   __shared__ CgScalars s_cg;
   const HookPre hpre = hook_prefetch(a.hook, rhs, &s_cg);
+  float al = 0.f, be = 0.f, gam = 0.f;
+  if constexpr (CG) {
+    __syncthreads();   // s_cg (hook_prefetch) visible to every thread
+    al = static_cast<float>(s_cg.alpha);
+    be = static_cast<float>(s_cg.beta);
+  }
 
   constexpr bool AL = fast_aligned(N);
   constexpr int SLOT_T = fast_slot_threads(N);
@@ -112,11 +131,78 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   };
   auto ld = [&](int off) -> float { return off >= 0 ? load_as<ST, float>(xin + off) : 0.f; };
 
+  // fused CG step: this thread's staging area (face k, value v at
+  // (6 k + v) SLOT_T + line: r, w, s, W, and p, x at owned faces)
+  float* stg = sm + a.ppb * PER + (in_slot ? slot : 0) * (36 * SLOT_T) + line;
+  const float* __restrict__ vr = CG ? a.cgv.r_in + toff : nullptr;
+  const float* __restrict__ vw = CG ? a.cgv.w_in + toff : nullptr;
+  const float* __restrict__ vs = CG ? a.cgv.s_in + toff : nullptr;
+  const float* __restrict__ vW = (CG && a.cgv.W) ? a.cgv.W + toff : nullptr;
+  float* __restrict__ vp = CG ? a.cgv.p + toff : nullptr;
+  float* __restrict__ vx = CG ? a.cgv.x + toff : nullptr;
+  // asynchronous loads of the state at the faces of element (f1, f2, f3);
+  // x1 lo is skipped when it was the previous element's x1 hi
+  auto fetch = [&](const FaceOffsets& fo, int f1, int f2, int f3, bool skip_lo1) {
+    const int off[6] = {fo.x1l, fo.x1h, fo.x2l, fo.x2h, fo.x3l, fo.x3h};
+    const bool own[6] = {f1 == 0, true, f2 == 0, true, f3 == 0, true};
+    static_for<0, 6>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if (k == 0 && skip_lo1) return;
+      const bool on = off[k] >= 0;
+      const int oo = on ? off[k] : 0;
+      cp_async4(stg + (6 * k + 0) * SLOT_T, vr + oo, on);
+      cp_async4(stg + (6 * k + 1) * SLOT_T, vw + oo, on);
+      cp_async4(stg + (6 * k + 2) * SLOT_T, vs + oo, on);
+      if (vW) cp_async4(stg + (6 * k + 3) * SLOT_T, vW + oo, on);
+      if (own[k]) {
+        cp_async4(stg + (6 * k + 4) * SLOT_T, vp + oo, on);
+        cp_async4(stg + (6 * k + 5) * SLOT_T, vx + oo, on);
+      }
+    });
+    cp_async_commit();
+  };
+  // the update of the previous iteration at those faces: u' into v[k]
+  auto consume = [&](const FaceOffsets& fo, int f1, int f2, int f3, bool skip_lo1, float* v) {
+    cp_async_wait_all();
+    const int off[6] = {fo.x1l, fo.x1h, fo.x2l, fo.x2h, fo.x3l, fo.x3h};
+    const bool own[6] = {f1 == 0, true, f2 == 0, true, f3 == 0, true};
+    float* __restrict__ vro = a.cgv.r_out + toff;
+    float* __restrict__ vso = a.cgv.s_out + toff;
+    float* __restrict__ vwz = a.cgv.w_zero + toff;
+    static_for<0, 6>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      if (k == 0 && skip_lo1) return;
+      v[k] = 0.f;
+      if (off[k] < 0) return;
+      const float r = stg[(6 * k + 0) * SLOT_T], w = stg[(6 * k + 1) * SLOT_T], sv = stg[(6 * k + 2) * SLOT_T];
+      const float Wv = vW ? stg[(6 * k + 3) * SLOT_T] : 1.f;
+      const float sn = fmaf(be, sv, w);
+      const float rn = fmaf(-al, sn, r);
+      const float un = Wv * rn;
+      v[k] = un;
+      if (own[k]) {
+        const int oo = off[k];
+        const float pn = fmaf(be, stg[(6 * k + 4) * SLOT_T], Wv * r);
+        vx[oo] = fmaf(al, pn, stg[(6 * k + 5) * SLOT_T]);
+        vp[oo] = pn;
+        vso[oo] = sn;
+        vro[oo] = rn;
+        vwz[oo] = 0.f;
+        gam = fmaf(un, rn, gam);
+      }
+    });
+  };
+
   FaceOffsets o = offsets(c1, c2, c3);
   float xlo1 = 0.f, xhi1 = 0.f, x2l = 0.f, x2h = 0.f, x3l = 0.f, x3h = 0.f;
+  bool carried = false;   // fused step: x1 lo is the previous element's x1 hi
   if (e < eend) {
-    xlo1 = ld(o.x1l); xhi1 = ld(o.x1h);
-    x2l = ld(o.x2l); x2h = ld(o.x2h); x3l = ld(o.x3l); x3h = ld(o.x3h);
+    if constexpr (CG) {
+      fetch(o, c1, c2, c3, false);
+    } else {
+      xlo1 = ld(o.x1l); xhi1 = ld(o.x1h);
+      x2l = ld(o.x2l); x2h = ld(o.x2h); x3l = ld(o.x3l); x3h = ld(o.x3h);
+    }
   }
   float carry = 0.f;
   bool have_carry = false;
@@ -126,6 +212,14 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   for (int t = 0; t < chunk; ++t) {
     const bool live = e < eend;
     float* S = base + (t & 1) * 4 * SF;
+    if constexpr (CG) {
+      if (live) {
+        float v[6];
+        consume(o, c1, c2, c3, carried, v);
+        if (!carried) xlo1 = v[0];
+        xhi1 = v[1]; x2l = v[2]; x2h = v[3]; x3l = v[4]; x3h = v[5];
+      }
+    }
     if (live) {
       S[qpad] = x2l + x2h;
       S[SF + qpad] = x2l - x2h;
@@ -159,9 +253,13 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
     if constexpr (!DZC)
       if (nlive && !m.uniform) prefetch_l1(dinv_r + (long long)(e + 1) * (N2 * R) + R * line);
     if (nlive) {
-      nlo1 = same ? xhi1 : ld(no.x1l);
-      nhi1 = ld(no.x1h);
-      n2l = ld(no.x2l); n2h = ld(no.x2h); n3l = ld(no.x3l); n3h = ld(no.x3h);
+      if constexpr (CG) {
+        fetch(no, n1, n2, n3, same);
+      } else {
+        nlo1 = same ? xhi1 : ld(no.x1l);
+        nhi1 = ld(no.x1h);
+        n2l = ld(no.x2l); n2h = ld(no.x2h); n3l = ld(no.x3l); n3h = ld(no.x3h);
+      }
     }
     const float4 mt = *reinterpret_cast<const float4*>(a.metric + (m.uniform ? 0 : 4 * (live ? e : 0)));
     const float d0 = mt.x, d1 = mt.y, d2 = mt.z, d3 = mt.w;
@@ -177,61 +275,83 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
       const float* dz = DZC ? nullptr : dinv_r + (m.uniform ? 0 : e * (N2 * R)) + R * (j + N * k);
       const float dzb = DZC ? fmaf(d3, a.tab.lam[k], fmaf(d2, a.tab.lam[j], lam_r * d0)) : 0.f;
       float* Ur = U + R * (j + N * k);
+      // pairs of points (i, i + 1) in packed two-lane FP32 arithmetic (one
+      // FMUL2/FFMA2 per pair); the x1 contraction keeps one two-lane
+      // accumulator per parity combination of a pair
+      float2 pEE = make_float2(0.f, 0.f), pOO = pEE, pEO = pEE;
+      const float2 cjd2v = make_float2(cjd2, cjd2), ckd3v = make_float2(ckd3, ckd3);
       static_for<0, NQ>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
         const float4 bv = *reinterpret_cast<const float4*>(Bs + 4 * q);
         const float4 cv = *reinterpret_cast<const float4*>(Cs + 4 * q);
         float4 dv = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (!DZC) dv = *reinterpret_cast<const float4*>(dz + 4 * q);
-        const float b[4] = {bv.x, bv.y, bv.z, bv.w};
-        const float c[4] = {cv.x, cv.y, cv.z, cv.w};
-        const float ev[4] = {dv.x, dv.y, dv.z, dv.w};
-        (void)ev;
-        float u[4] = {0.f, 0.f, 0.f, 0.f};
-        static_for<0, 4>([&](auto lc) {
-          constexpr int l = decltype(lc)::value;
-          constexpr int i = 4 * q + l;
-          if constexpr (i < N) {
-            float F = a.tab.c[i] * (i < NE ? Ap : Am);
-            F = fmaf(cjd2, b[l], F);
-            F = fmaf(ckd3, c[l], F);
-            float inv;
-            if constexpr (DZC) inv = __fdividef(1.0f, fmaf(d1, a.tab.lam[i], dzb));
-            else inv = ev[l];
-            u[l] = F * inv;
-            if constexpr (i < NE) Pp = fmaf(a.tab.c[i], u[l], Pp);
-            else Pm = fmaf(a.tab.c[i], u[l], Pm);
+        (void)dv;
+        float2 uh[2];
+        static_for<0, 2>([&](auto hc) {
+          constexpr int hh = decltype(hc)::value;
+          constexpr int i0 = 4 * q + 2 * hh, i1 = i0 + 1;
+          if constexpr (i0 < N) {
+            constexpr bool e0 = i0 < NE, e1 = i1 < NE, v1 = i1 < N;
+            const float c0 = a.tab.c[i0], c1v = v1 ? a.tab.c[i1] : 0.f;
+            // the second lane of the last pair of an odd row lies in the row
+            // padding, which no thread writes: it takes zeros
+            const float b0 = hh == 0 ? bv.x : bv.z, b1 = v1 ? (hh == 0 ? bv.y : bv.w) : 0.f;
+            const float k0 = hh == 0 ? cv.x : cv.z, k1 = v1 ? (hh == 0 ? cv.y : cv.w) : 0.f;
+            float2 F = __fmul2_rn(make_float2(c0, c1v), make_float2(e0 ? Ap : Am, e1 ? Ap : Am));
+            F = __ffma2_rn(cjd2v, make_float2(b0, b1), F);
+            F = __ffma2_rn(ckd3v, make_float2(k0, k1), F);
+            float2 inv;
+            if constexpr (DZC) {
+              const float2 den = __ffma2_rn(make_float2(d1, d1),
+                                            make_float2(a.tab.lam[i0], v1 ? a.tab.lam[i1] : 0.f),
+                                            make_float2(dzb, dzb));
+              inv = make_float2(dz_recip(den.x), v1 ? dz_recip(den.y) : 0.f);
+            } else {
+              inv = make_float2(hh == 0 ? dv.x : dv.z, v1 ? (hh == 0 ? dv.y : dv.w) : 0.f);
+            }
+            const float2 u = __fmul2_rn(F, inv);
+            uh[hh] = u;
+            const float2 cc = make_float2(c0, c1v);
+            if constexpr (e0 && e1) pEE = __ffma2_rn(cc, u, pEE);
+            else if constexpr (!e0 && !e1) pOO = __ffma2_rn(cc, u, pOO);
+            else pEO = __ffma2_rn(cc, u, pEO);
+          } else {
+            uh[hh] = make_float2(0.f, 0.f);
           }
         });
-        *reinterpret_cast<float4*>(Ur + 4 * q) = make_float4(u[0], u[1], u[2], u[3]);
+        *reinterpret_cast<float4*>(Ur + 4 * q) = make_float4(uh[0].x, uh[0].y, uh[1].x, uh[1].y);
       });
+      Pp = (pEE.x + pEE.y) + pEO.x;
+      Pm = (pOO.x + pOO.y) + pEO.y;
     }
     slot_sync();
 
     if (live) {
       const int i = lo_i, mm = hi_i;
-      float Qp = 0.f, Qm = 0.f, Rp = 0.f, Rm = 0.f;
       const float* Uq = U + i + R * N * mm;   // (i, j = mo, k = mm): stride R
       const float* Ur2 = U + i + R * mm;       // (i, j = mm, k = mo): stride R N
+      // the x2 and x3 contractions as one two-lane accumulator per parity
+      float2 QRp = make_float2(0.f, 0.f), QRm = QRp;
       static_for<0, N>([&](auto mc) {
         constexpr int mo = decltype(mc)::value;
-        const float uq = Uq[R * mo];
-        const float ur = Ur2[R * N * mo];
-        if constexpr (mo < NE) { Qp = fmaf(a.tab.c[mo], uq, Qp); Rp = fmaf(a.tab.c[mo], ur, Rp); }
-        else                   { Qm = fmaf(a.tab.c[mo], uq, Qm); Rm = fmaf(a.tab.c[mo], ur, Rm); }
+        const float2 uu = make_float2(Uq[R * mo], Ur2[R * N * mo]);
+        const float2 cm = make_float2(a.tab.c[mo], a.tab.c[mo]);
+        if constexpr (mo < NE) QRp = __ffma2_rn(cm, uu, QRp);
+        else QRm = __ffma2_rn(cm, uu, QRm);
       });
       {  // x2 faces, node (i, k = mm)
         const float Sv = S[qpad], Dv = S[SF + qpad];
-        const float sum = d2 * (hs * Sv - 2.f * Qp), dif = d2 * (hd * Dv - 2.f * Qm);
-        if (o.x2l >= 0) red_add(yout + o.x2l, 0.5f * (sum + dif));
-        if (o.x2h >= 0) red_add(yout + o.x2h, 0.5f * (sum - dif));
+        const float sum = d2 * (hs * Sv - 2.f * QRp.x), dif = d2 * (hd * Dv - 2.f * QRm.x);
+        red_add_if(o.x2l >= 0, yout + max(o.x2l, 0), 0.5f * (sum + dif));
+        red_add_if(o.x2h >= 0, yout + max(o.x2h, 0), 0.5f * (sum - dif));
         dot = fmaf(Sv, sum, fmaf(Dv, dif, dot));
       }
       {  // x3 faces, node (i, j = mm)
         const float Sv = S[2 * SF + qpad], Dv = S[3 * SF + qpad];
-        const float sum = d3 * (hs * Sv - 2.f * Rp), dif = d3 * (hd * Dv - 2.f * Rm);
-        if (o.x3l >= 0) red_add(yout + o.x3l, 0.5f * (sum + dif));
-        if (o.x3h >= 0) red_add(yout + o.x3h, 0.5f * (sum - dif));
+        const float sum = d3 * (hs * Sv - 2.f * QRp.y), dif = d3 * (hd * Dv - 2.f * QRm.y);
+        red_add_if(o.x3l >= 0, yout + max(o.x3l, 0), 0.5f * (sum + dif));
+        red_add_if(o.x3h >= 0, yout + max(o.x3h, 0), 0.5f * (sum - dif));
         dot = fmaf(Sv, sum, fmaf(Dv, dif, dot));
       }
       {  // x1 faces, node (j, k) = line
@@ -239,17 +359,21 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
         const float rlo = 0.5f * (sum + dif), rhi = 0.5f * (sum - dif);
         dot = fmaf(S1, sum, fmaf(D1, dif, dot));
         // lo plane: the previous element of the run left its share in
-        // `carry`; plane 0 has no other contributor; else another run adds
-        if (o.x1l >= 0) {
-          if (have_carry) store_from<ST, float>(yout + o.x1l, carry + rlo);
-          else if (c1 == 0) store_from<ST, float>(yout + o.x1l, rlo);
-          else red_add(yout + o.x1l, rlo);
+        // `carry`; plane 0 has no other contributor (stored); else another
+        // run adds
+        {
+          const bool on = o.x1l >= 0, st = on && (have_carry || c1 == 0);
+          ST* dst = yout + max(o.x1l, 0);
+          st_if(st, dst, have_carry ? carry + rlo : rlo);
+          red_add_if(on && !st, dst, rlo);
         }
         // hi plane: kept for the next element of the run; the top plane has
-        // no other contributor; else another run adds
-        if (o.x1h >= 0 && !(kCarry && same)) {
-          if (c1 + 1 == N1e) store_from<ST, float>(yout + o.x1h, rhi);
-          else red_add(yout + o.x1h, rhi);
+        // no other contributor (stored); else another run adds
+        {
+          const bool on = o.x1h >= 0 && !(kCarry && same), st = on && c1 + 1 == N1e;
+          ST* dst = yout + max(o.x1h, 0);
+          st_if(st, dst, rhi);
+          red_add_if(on && !st, dst, rhi);
         }
         carry = rhi;
         have_carry = kCarry && same;
@@ -258,12 +382,18 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
     o = no;
     c1 = n1; c2 = n2; c3 = n3;
     ++e;
-    xlo1 = nlo1; xhi1 = nhi1;
-    x2l = n2l; x2h = n2h; x3l = n3l; x3h = n3h;
+    if constexpr (CG) {
+      carried = same;
+      if (same) xlo1 = xhi1;
+    } else {
+      xlo1 = nlo1; xhi1 = nhi1;
+      x2l = n2l; x2h = n2h; x3l = n3l; x3h = n3h;
+    }
   }
 
   grid_dep_launch();   // the next kernel's blocks may take this block's place
-  if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, dot, hpre, &s_cg);
+  if constexpr (CG) hook_finish_cg(a.hook, a.cgv.gpartials, rhs, dot, gam, &s_cg);
+  else if (a.hook.partials != nullptr) hook_finish(a.hook, rhs, dot, hpre, &s_cg);
 }
 
 }  // namespace hdg

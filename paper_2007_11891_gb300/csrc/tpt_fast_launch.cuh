@@ -21,17 +21,26 @@ namespace hdg {
     default: break;                                                             \
   }
 
-template <int N, bool DZC>
+// Dynamic shared memory of the element-run kernel with `ppb` slots: the
+// staged faces and eigenspace solution per slot, and with the fused CG step
+// (CGM = 1) each thread's staging area of 36 values.
+template <int N, int CGM>
+constexpr size_t fast_smem_bytes(int ppb) {
+  return (size_t)ppb * (tpt_smem_per_pencil<float, N>() + (CGM ? 36 * fast_slot_threads(N) : 0)) * sizeof(float);
+}
+
+template <int N, bool DZC, int CGM = 0>
 int fast_occupancy(int ppb) {
   static int cached[65] = {0};
   const int key = ppb < 64 ? ppb : 64;
   if (cached[key] > 0) return cached[key];
   const int threads = fast_threads(N, ppb);
-  const size_t smem = (size_t)ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
+  const size_t smem = fast_smem_bytes<N, CGM>(ppb);
   if (smem > kSmemOptIn)
-    cudaFuncSetAttribute(tpt_fast_kernel<N, DZC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, float, CGM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpt_fast_kernel<N, DZC>, threads, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tpt_fast_kernel<N, DZC, float, CGM>, threads, smem) !=
           cudaSuccess ||
       nb < 1) {
     cudaGetLastError();
@@ -41,16 +50,16 @@ int fast_occupancy(int ppb) {
   return nb;
 }
 
-template <int N, bool DZC, typename ST>
+template <int N, bool DZC, typename ST, int CGM = 0>
 cudaError_t fast_launch(const TptArgs<float, ST>& a, int nrhs, cudaStream_t s) {
   const long long nelem = a.npencils * a.mesh.ne[0];
   if (nelem <= 0) return cudaSuccess;
   if (a.chunk < 1 || a.ppb < 1) return cudaErrorInvalidValue;
   const int threads = fast_threads(N, a.ppb);
-  const size_t smem = (size_t)a.ppb * tpt_smem_per_pencil<float, N>() * sizeof(float);
+  const size_t smem = fast_smem_bytes<N, CGM>(a.ppb);
   if (threads > fast_max_threads(N) || (fast_aligned(N) && a.ppb > 15)) return cudaErrorInvalidConfiguration;
   if (smem > kSmemOptIn) {
-    cudaError_t e = cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, ST>,
+    cudaError_t e = cudaFuncSetAttribute(tpt_fast_kernel<N, DZC, ST, CGM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -68,14 +77,19 @@ cudaError_t fast_launch(const TptArgs<float, ST>& a, int nrhs, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tpt_fast_kernel<N, DZC, ST>, a);
+    return cudaLaunchKernelEx(&cfg, tpt_fast_kernel<N, DZC, ST, CGM>, a);
   }
-  tpt_fast_kernel<N, DZC, ST><<<grid, threads, smem, s>>>(a);
+  tpt_fast_kernel<N, DZC, ST, CGM><<<grid, threads, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int N, typename ST>
 cudaError_t fast_dispatch_dz(const TptArgs<float, ST>& a, int nrhs, cudaStream_t s) {
+  if constexpr (std::is_same<ST, float>::value) {
+    if (a.cg == 1)
+      return a.dinv ? fast_launch<N, false, ST, 1>(a, nrhs, s) : fast_launch<N, true, ST, 1>(a, nrhs, s);
+  }
+  if (a.cg != 0) return cudaErrorInvalidValue;
   return a.dinv ? fast_launch<N, false, ST>(a, nrhs, s) : fast_launch<N, true, ST>(a, nrhs, s);
 }
 

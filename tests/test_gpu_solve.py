@@ -276,37 +276,45 @@ def test_polynomial_reproduction_high_degree(p, inner):
 
 
 @pytest.mark.parametrize("inner", ["fp32", "fp64"])
-@pytest.mark.parametrize("bc", [(0,) * 6, (1, 0, 1, 0, 1, 0), (0, 1, 1, 1, 0, 1)])
-def test_fused_and_two_kernel_cg_agree(inner, bc):
+@pytest.mark.parametrize("ne,bc,p", [((5, 4, 3), (0,) * 6, 4), ((5, 4, 3), (1, 0, 1, 0, 1, 0), 4),
+                                     ((5, 4, 3), (0, 1, 1, 1, 0, 1), 4), ((9, 7, 5), (1, 1, 0, 1, 1, 0), 3)])
+def test_fused_and_two_kernel_cg_agree(inner, ne, bc, p):
     # the fused CG step (the operator launch applies the previous update to
     # the face values it reads; each face value has one owner, also on
-    # Neumann sides), as one persistent cooperative launch per inner solve and
-    # as one launch per iteration, against the operator + update kernel pair:
-    # all reach the tolerance on the oracle's residual, with about the same
-    # iteration count (same iterates in exact arithmetic)
+    # Neumann sides): in the tile kernel as one persistent cooperative launch
+    # per inner solve and as one launch per iteration, and in the FP32
+    # element-run kernel (runs crossing pencils, the x1 face between two
+    # elements of a run updated once), against the operator + update kernel
+    # pair: all reach the tolerance on the oracle's residual, with about the
+    # same iteration count (same iterates in exact arithmetic)
     from paper_2007_11891_gb300 import HDG
-    ne, p, lam = (5, 4, 3), 4, 0.7
+    lam = 0.7
     grid = _stretched(ne, 23)
     pr = Problem(ne, grid, bc, p, 25.0, lam)
     f = hdg_inputs.gaussian(pr.mesh.n_elem * (p + 1) ** 3, 24)
+    cases = [("persistent", "tiles"), ("fused", "tiles"), ("two_kernel", "auto")]
+    if inner == "fp32":
+        cases.append(("fused", "runs"))
     out = {}
-    for variant in ("persistent", "fused", "two_kernel"):
+    for variant, op in cases:
         h = HDG(ne, grid, bc, p, 25.0)
         h.set_cg_variant(variant)
+        h.set_operator_variant(op)
         tr, u, info = h.solve(torch.tensor(f, device="cuda"), lam, tol=1e-10, inner=inner)
         assert info[0]["status"] == "OK"
         assert _oracle_residual(pr, tr.cpu().numpy(), f=f) <= 1e-10
-        out[variant] = (info[0]["iterations"], u)
-    it_t = out["two_kernel"][0]
-    ref = out["two_kernel"][1].abs().max().item()
-    for variant in ("persistent", "fused"):
-        it_f = out[variant][0]
-        assert abs(it_f - it_t) <= max(3, 0.05 * it_t), (variant, it_f, it_t)
-        assert (out[variant][1] - out["two_kernel"][1]).abs().max().item() <= 1e-8 * ref
-    # the persistent and the per-launch fused step run the same arithmetic in
-    # the same order: the same iterations, bitwise the same solution
-    assert out["persistent"][0] == out["fused"][0]
-    assert torch.equal(out["persistent"][1], out["fused"][1])
+        out[(variant, op)] = (info[0]["iterations"], u)
+    base = out[("two_kernel", "auto")]
+    ref = base[1].abs().max().item()
+    for key in cases[:2] + cases[3:]:
+        it_f = out[key][0]
+        assert abs(it_f - base[0]) <= max(3, 0.05 * base[0]), (key, it_f, base[0])
+        assert (out[key][1] - base[1]).abs().max().item() <= 1e-8 * ref
+    # the persistent and the per-launch fused step of the tile kernel run the
+    # same arithmetic in the same order: the same iterations, bitwise the same
+    # solution
+    assert out[("persistent", "tiles")][0] == out[("fused", "tiles")][0]
+    assert torch.equal(out[("persistent", "tiles")][1], out[("fused", "tiles")][1])
 
 
 @pytest.mark.parametrize("inner", ["fp64", "fp32"])
