@@ -295,11 +295,17 @@ def run_ours(args, rank, world, local_rank):
     ne_tot = ne[0] * ne[1] * ne[2]
     faces = T // (n * n)
 
-    def alu(kind, name, flops, avg_s, note):
+    def alu(kind, name, flops, avg_s, note, pipe_ops=None):
         ach = flops / avg_s / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None, "peak_source": fp64_src, "avg_launch_us": avg_s * 1e6,
-                "algorithmic_flops_per_launch": flops, "flops_counted": note}
+        out = {"kernel": name, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+               "frac": ach / fp64_peak, "traffic": None, "peak_source": fp64_src, "avg_launch_us": avg_s * 1e6,
+               "algorithmic_flops_per_launch": flops, "flops_counted": note}
+        if pipe_ops is not None:
+            # FP64 pipe operations (an FMA, a multiply and an add each take one
+            # issue slot of the pipe) against its rate, half the FMA flop rate
+            out["fp64_pipe_ops_per_launch"] = pipe_ops
+            out["frac_fp64_pipe_ops"] = pipe_ops / avg_s / (fp64_peak * 1e12 / 2.0)
+        return out
 
     fp32_iters = pinfo[0]["iterations"] + pinfo[0]["outer"]   # operator applications of the inner CGs
 
@@ -338,7 +344,9 @@ def run_ours(args, rank, world, local_rank):
         if kind == "op_fp64":
             return alu(kind, "tpt_tile_kernel<double> (operator, FP64, refinement residual)",
                        (12.0 * n ** 3 + 24.0 * n ** 2) * ne_tot, avg_s,
-                       "executed: 12 n^3 + 24 n^2 per element (parity-split expansion and contraction)")
+                       "executed: 12 n^3 + 24 n^2 per element (parity-split expansion and contraction); "
+                       "pipe operations 7 n^3 + 42 n^2 per element",
+                       pipe_ops=(7.0 * n ** 3 + 42.0 * n ** 2) * ne_tot)
         if kind == "face":
             return alu(kind, "face_rows_kernel (FP64 face transforms)", 2.0 * n ** 3 * faces, avg_s,
                        "executed: 2 n^3 per face (parity-split line transforms, rows and columns)")

@@ -274,8 +274,9 @@ hdg_status hdg_autotune(hdg_ctx* ctx, int nrhs, const double* h_lambda, hdg_prec
 hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
 
 /* Tuning (not part of the method): work split of the operator kernel.
- * 0 automatic (element tiles for FP64 arithmetic and BF16 storage, element
- * runs for FP32: the choice that measured fastest); 2 element tiles (CTAs of n^2 G threads take
+ * 0 automatic, the choice that measured fastest: element tiles for BF16
+ * storage, for FP32 at n = 10 and 12..16 and for FP64 with one right-hand
+ * side; element runs otherwise; 2 element tiles (CTAs of n^2 G threads take
  * tiles of consecutive elements in element order, one face node / x1-line
  * per thread; hdg_set_x1_segment sets the elements per tile, rounded to a
  * multiple of G); 1 element runs (one thread per x1-line, runs of elements

@@ -237,15 +237,22 @@ hdg_status ensure_dinv(hdg_ctx* c, int nrhs, const double* lam, cudaStream_t s, 
   return HDG_OK;
 }
 
-// Whether the apply of arithmetic T / storage ST runs the element-tile
-// kernel.  Automatic choice, from solve and apply timings on this part: the
-// tiles for FP64 arithmetic and BF16 storage, the element runs for FP32
-// (shorter per-element latency; equal or faster on every measured mesh).
+// Whether the apply of arithmetic T / storage ST with nrhs right-hand sides
+// runs the element-tile kernel.  Automatic choice, from apply and solve
+// timings on this part (32^3 applies at p = 2..16; solves on 8^3..32^3
+// meshes, single and batched): BF16 storage: tiles (1.4-1.6x faster);
+// FP32: tiles at n = 10 and 12..16, where the element-run slots are packed
+// (n = 10) or the tile rows are padded conflict-free (up to 1.6x faster at
+// p = 13), element runs at the other degrees (shorter per-element latency,
+// 5-40 % faster); FP64: tiles for one right-hand side (3-15 % faster at
+// 16^3 and 32^3), element runs for batches (12 % faster at 16 rhs).
 template <typename T, typename ST>
-bool use_tiles(const hdg_ctx* c) {
+bool use_tiles(const hdg_ctx* c, int nrhs) {
   if (c->op_variant == 1 || c->op_variant == 3) return false;
   if (c->op_variant == 2) return true;
-  return sizeof(T) == 8 || sizeof(ST) == 2;
+  if (sizeof(ST) == 2) return true;
+  if (sizeof(T) == 8) return nrhs <= 1;
+  return c->n == 10 || (c->n >= 12 && c->n <= 16);
 }
 
 template <typename T, typename ST>
@@ -273,7 +280,7 @@ hdg::TptArgs<T, ST> base_args(const hdg_ctx* c, const T* dinv, int nrhs, int mod
   a.sms = c->sms;
   a.tile = c->seg_override;   // elements per tile of the tile kernel (0 = automatic)
   // apply kernel: element tiles (tpt_tile.cuh) or element runs (use_tiles)
-  if (mode == hdg::TPT_APPLY && use_tiles<T, ST>(c)) a.variant = 3;
+  if (mode == hdg::TPT_APPLY && use_tiles<T, ST>(c, nrhs)) a.variant = 3;
   if (c->op_variant == 3) a.variant = 4;   // runtime-degree kernel, every mode
   // FP32 apply: equal contiguous runs, one per slot of a resident wave (per
   // right-hand side: the wave is shared by the batch)
@@ -453,7 +460,7 @@ hdg_status cg_fused_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* Wt,
   T* S[2] = {wsp<T>(c, W_S), wsp<T>(c, W_S2)};
   T* Wb[3] = {wsp<T>(c, W_Q), wsp<T>(c, W_W2), wsp<T>(c, W_W3)};
   hdg::TptArgs<T, T> a = base_args<T, T>(c, dinv, nrhs);
-  if (sizeof(T) == 4 && !use_tiles<T, T>(c)) {
+  if (sizeof(T) == 4 && !use_tiles<T, T>(c, nrhs)) {
     // the element-run kernel: runs sized for its own occupancy with the
     // staging areas of the fused step
     a.variant = 0;
@@ -1104,7 +1111,7 @@ hdg_status hdg_autotune(hdg_ctx* c, int nrhs, const double* h_lambda, hdg_precis
   HDG_CUDA(cudaMemsetAsync(c->ws[W_XHAT].p, 0x3c, esz * tot, s));   // finite, non-zero pattern
   // candidate segment lengths (distinct splits of the x1-pencils) and slots;
   // for the tile kernel: elements per tile, no slots
-  const bool tiles = prec == HDG_FP64 ? use_tiles<double, double>(c) : use_tiles<float, float>(c);
+  const bool tiles = prec == HDG_FP64 ? use_tiles<double, double>(c, nrhs) : use_tiles<float, float>(c, nrhs);
   std::vector<int> segs = {0};
   if (tiles) {
     for (int e : {2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 20, 24, 28, 32}) segs.push_back(e);

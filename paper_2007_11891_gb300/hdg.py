@@ -111,10 +111,10 @@ class HDG:
         _capi.check(_capi.lib().hdg_set_dz_mode(self._h, code), "hdg_set_dz_mode")
 
     def set_operator_variant(self, variant):
-        """Operator kernel: 'auto' (tiles for FP64 and BF16 storage, runs for
-        FP32), 'tiles' (element tiles), 'runs' (one thread per x1-line in
-        element runs) or 'generic' (the runtime-degree kernel that degrees
-        above 16 use, any degree)."""
+        """Operator kernel: 'auto' (the measured fastest per precision,
+        degree and batch size), 'tiles' (element tiles), 'runs' (one thread
+        per x1-line in element runs) or 'generic' (the runtime-degree kernel
+        that degrees above 16 use, any degree)."""
         code = {"auto": 0, "runs": 1, "tiles": 2, "generic": 3}[variant]
         _capi.check(_capi.lib().hdg_set_operator_variant(self._h, code), "hdg_set_operator_variant")
 
