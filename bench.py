@@ -43,7 +43,7 @@ FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the same kernel and workload (cold caches); None when the
 # kernel changed after the capture
-TRAFFIC_BYTES = {"op_fp32": None}
+TRAFFIC_BYTES = {"op_fp32": 6827008}   # tpt_fast_kernel<9, 1, float, 0> in the CG loop: read 6.83 MB, write 0
 
 
 def peaks():
@@ -329,7 +329,8 @@ def run_ours(args, rank, world, local_rank):
             name = ("FP32 fused CG step (operator + update in one launch per iteration)" if fused else
                     "tpt_fast_kernel<float> (FP32 operator of the inner CG, element runs)")
             return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / pk["hbm_gbs"], "traffic": TRAFFIC_BYTES["op_fp32"], "peak_source": "of " + src,
+                    "frac": ach / pk["hbm_gbs"], "traffic": None if fused else TRAFFIC_BYTES["op_fp32"],
+                    "peak_source": "of " + src,
                     "launches_per_solve": c["launches"], "cg_iterations_per_solve": fp32_iters,
                     "avg_launch_us": it_s * 1e6, "algorithmic_bytes_per_launch": byts,
                     "bytes_counted": ("9 T x 4 B per CG iteration, the minimum of a CG iteration (operator: read "
