@@ -15,11 +15,12 @@ x1- and x2-faces never cross a slab boundary.
 
 This module is bookkeeping and communication only: the sub-meshes, the map
 of local trace entries to the global trace layout of include/hdg.h, which
-rank owns an interface plane (for inner products), and the exchange, done
-as an all-reduce (sum) over the two ranks that share the plane, so that the
+rank owns an interface plane (for inner products), the exchange, done as an
+all-reduce (sum) over the two ranks that share the plane, so that the
 collective library adds the two partial values (both ranks receive the same
-sum, bitwise).  The local operator is whatever the caller passes: the
-library's apply on each rank's own GPU.
+sum, bitwise), and the partitioned CG, whose inner products add the ranks'
+owned shares in one all-reduce per iteration.  The local operator is
+whatever the caller passes: the library's apply on each rank's own GPU.
 """
 import numpy as np
 
@@ -149,6 +150,58 @@ class SlabPartition:
         """y = K x on the local slab: the rank's own operator, then the
         interface exchange."""
         return self.exchange(local_apply(x_local))
+
+    def dots(self, pairs):
+        """Global inner products of pairs of local vectors (torch tensors):
+        each rank sums its owned entries (an interface value is owned by the
+        rank below it), and one all-reduce of the whole list of scalars adds
+        the ranks' shares.  Returns a float64 tensor of len(pairs)."""
+        import torch
+        import torch.distributed as dist
+        own = torch.as_tensor(self.owned, device=pairs[0][0].device)
+        vals = torch.stack([(a[own].double() * b[own].double()).sum() for a, b in pairs])
+        if self.world > 1:
+            dist.all_reduce(vals, op=dist.ReduceOp.SUM)
+        return vals
+
+    def cg(self, local_apply, b_local, tol=1e-10, max_iter=1000, w_local=None):
+        """Solve K x = b on the partitioned operator with the single-reduction
+        preconditioned CG (Chronopoulos-Gear; the iterates of the textbook
+        preconditioned CG in exact arithmetic): per iteration one operator
+        application (the rank's own apply and the interface exchange) and one
+        all-reduce of three scalars (r . u, w . u, r . r).  w_local: the
+        diagonal preconditioner on the local entries, or None.  Every rank
+        takes the same decisions (the scalars are identical after the
+        all-reduce).  Returns (x_local, iterations, relative residual
+        ||b - K x|| / ||b|| as tracked by the recurrence)."""
+        import torch
+        W = (lambda v: v) if w_local is None else (lambda v: w_local * v)
+        x = torch.zeros_like(b_local)
+        r = b_local.clone()
+        u = W(r)
+        w = self.apply(local_apply, u)
+        gam, dlt, rr = [float(v) for v in self.dots([(r, u), (w, u), (r, r)])]
+        bb = rr
+        if bb == 0.0:
+            return x, 0, 0.0
+        p, s = u.clone(), w.clone()
+        alpha = gam / dlt
+        it = 0
+        while it < max_iter:
+            x += alpha * p
+            r -= alpha * s
+            it += 1
+            u = W(r)
+            w = self.apply(local_apply, u)
+            gam_new, dlt, rr = [float(v) for v in self.dots([(r, u), (w, u), (r, r)])]
+            if rr <= tol * tol * bb:
+                break
+            beta = gam_new / gam
+            alpha = gam_new / (dlt - beta * gam_new / alpha)
+            p = u + beta * p
+            s = w + beta * s
+            gam = gam_new
+        return x, it, (rr / bb) ** 0.5
 
     # -- layout helpers -------------------------------------------------------------
     def scatter(self, x_global):

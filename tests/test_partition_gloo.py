@@ -93,6 +93,58 @@ def test_slab_partition_apply_equals_whole_mesh(world):
         assert d == pytest.approx(float(ref @ z), rel=1e-12)
 
 
+def _cg_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    from oracle.solver import Problem
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ne, bc, p = MESH["ne"], MESH["bc"], MESH["p"]
+    grid = _grid(ne)
+    part = SlabPartition(ne, grid, bc, p, world, rank).init_groups()
+    local = Problem(part.local_ne, part.local_grid, part.local_bc, p, MESH["tau"], MESH["lam"])
+    # b = K x* of the whole mesh, computed by the oracle on every rank
+    whole = Problem(ne, grid, bc, p, MESH["tau"], MESH["lam"])
+    xs = np.random.default_rng(21).uniform(-1.0, 1.0, whole.mesh.n_trace)
+    b = torch.tensor(part.scatter(whole.apply(xs)))
+    x, it, rel = part.cg(lambda v: torch.tensor(local.apply(v.numpy())), b, tol=1e-12, max_iter=500)
+    q.put((rank, part.global_index, x.numpy(), it, rel))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_slab_partition_cg_solves_the_whole_mesh_system(world):
+    # the partitioned CG (local applies + interface exchange, one all-reduce
+    # of the inner products per iteration) recovers x* from b = K x* of the
+    # whole mesh; every rank takes the same number of iterations, and the
+    # two copies of an interface value agree bitwise
+    import torch.multiprocessing as mp
+    from oracle.solver import Problem
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_cg_worker, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    out = sorted((q.get(timeout=300) for _ in procs), key=lambda t: t[0])
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    ne, bc, p = MESH["ne"], MESH["bc"], MESH["p"]
+    whole = Problem(ne, _grid(ne), bc, p, MESH["tau"], MESH["lam"])
+    xs = np.random.default_rng(21).uniform(-1.0, 1.0, whole.mesh.n_trace)
+    x = np.full(whole.mesh.n_trace, np.nan)
+    for _, gi, xl, it, rel in out:
+        held = ~np.isnan(x[gi])
+        assert np.array_equal(x[gi[held]], xl[held])
+        x[gi] = xl
+        assert it == out[0][3] and rel <= 1e-12
+    assert not np.any(np.isnan(x))
+    assert np.abs(x - xs).max() <= 1e-9 * np.abs(xs).max()
+
+
 def test_slab_bounds_and_local_layout():
     assert slab_bounds(5, 2) == [(0, 3), (3, 5)]
     assert slab_bounds(7, 3) == [(0, 3), (3, 5), (5, 7)]
