@@ -350,3 +350,52 @@ def test_degree_above_sixteen_operator_is_symmetric_positive():
     ab, ba = float(torch.dot(b, ya)), float(torch.dot(a, h.apply(b, 0.5, basis="transformed")))
     assert abs(ab - ba) <= 1e-11 * max(abs(ab), 1.0)
     assert float(torch.dot(a, ya)) > 0
+
+
+def test_batched_configuration_full_size():
+    # the batched workload at its full size (24^3, p = 7, 64 right-hand
+    # sides, lambda from {0.1, 1, 100}): every right-hand side reaches the
+    # FP64 residual 1e-10 (the solver's own FP64 check, nodal basis), and
+    # sampled right-hand sides agree with solves by the FP64 inner CG
+    from paper_2007_11891_gb300 import HDG
+    cfg = hdg_inputs.WORKLOADS["batched24_p7"]
+    ne, p, nrhs = cfg["ne"], cfg["p"], cfg["nrhs"]
+    h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, p, hdg_inputs.TAU_HAT)
+    lams = hdg_inputs.batch_lambdas(nrhs)
+    F = torch.tensor(np.stack([hdg_inputs.gaussian(h.volume_size, 11894 + r) for r in range(nrhs)]), device="cuda")
+    tr, _, info = h.solve(F, lams, tol=1e-10, inner="fp32", return_u=False)
+    assert all(i["status"] == "OK" and i["rel_residual"] <= 1e-10 for i in info)
+    pick = [int(np.argmin(lams)), int(np.argmax(lams)), nrhs - 1]
+    t64, _, info64 = h.solve(F[pick], lams[pick], tol=1e-12, inner="fp64", return_u=False)
+    assert all(i["status"] == "OK" for i in info64)
+    for k, r in enumerate(pick):
+        scale = float(t64[k].abs().max())
+        assert float((tr[r] - t64[k]).abs().max()) <= 1e-8 * scale
+
+
+def test_adjoint_configuration_full_size_finite_difference():
+    # the differentiation workload's mesh at its full size (32^3, p = 6,
+    # lambda = 5): dL/dlambda from the adjoint solve against a central finite
+    # difference of two forward solves.  The workload's own loss
+    # ||u - u_t||^2 changes by ~1e-12 of itself over a usable step, below
+    # the solves' accuracy, so the check uses the linear functional
+    # L = g . u (g ~ N(0, 1)), whose dL/du = g drives the same adjoint
+    # machinery; relative step 1e-3 (truncation ~1e-6), solves to 1e-12
+    from paper_2007_11891_gb300 import HDG
+    cfg = hdg_inputs.WORKLOADS["adjoint32_p6"]
+    ne, p, lam = cfg["ne"], cfg["p"], cfg["lam"]
+    h = HDG(ne, hdg_inputs.grid_lines(ne), (0,) * 6, p, hdg_inputs.TAU_HAT)
+    f = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11897), device="cuda")
+    g = torch.tensor(hdg_inputs.gaussian(h.volume_size, 11898), device="cuda")
+
+    def loss(lm):
+        _, u, info = h.solve(f, lm, tol=1e-12, inner="fp32")
+        assert info[0]["status"] == "OK"
+        return float(torch.dot(g, u)), u
+
+    _, u = loss(lam)
+    _, gl, info = h.solve_adjoint(u, g, lam, tol=1e-12, inner="fp32")
+    assert info[0]["status"] == "OK"
+    dl = 1e-3 * lam
+    fd = (loss(lam + dl)[0] - loss(lam - dl)[0]) / (2.0 * dl)
+    assert abs(float(gl[0]) - fd) <= 1e-4 * abs(fd)
