@@ -290,11 +290,10 @@ hdg_status hdg_set_dz_mode(hdg_ctx* ctx, int mode);
 hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant);
 
 /* Tuning (not part of the method): how an inner CG iteration runs.
- *   3 (default) as 1, two kernels per iteration (measured fastest on the
- *     meshes of 8^3 to 32^3 elements tried, in FP32 and FP64);
- *   0 with the element-tile operator kernel (hdg_set_operator_variant 0
- *     or 2; the fused step always uses the tile kernel): the whole inner CG in one
- *     cooperative launch of that kernel (every CTA resident; per iteration,
+ *   3 (default) as 1, two kernels per iteration (measured fastest or within
+ *     10 % on the meshes of 8^3 to 32^3 elements tried, in FP32 and FP64);
+ *   0 the whole inner CG in one cooperative launch of the element-tile
+ *     kernel (every CTA resident; per iteration,
  *     each CTA applies the CG update of the previous iteration to every face
  *     value it reads -- each face value's one owner stores the new x, p, r,
  *     s -- applies the operator to the new search direction, and after one
@@ -302,7 +301,10 @@ hdg_status hdg_set_operator_variant(hdg_ctx* ctx, int variant);
  *     sums in the same order); where a cooperative launch is not possible,
  *     as variant 2;
  *   2 the same fused step, one launch per iteration (the last CTA of each
- *     launch forms the step scalars), launched from a CUDA graph;
+ *     launch forms the step scalars), launched from a CUDA graph; in the
+ *     FP32 element-run kernel (the state of the faces of the next element
+ *     staged asynchronously while the current one computes) where the
+ *     automatic operator choice is the element runs, else in the tiles;
  *   1 two kernels per iteration: the operator, then the vector update.
  * All compute the same CG iterates in exact arithmetic.  A grid barrier that
  * waits too long (CTAs not co-resident) ends the kernel and the solve
