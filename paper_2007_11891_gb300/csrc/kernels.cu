@@ -584,46 +584,72 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
   // write them: they are loaded while the operator's last block is still
   // reducing.  w, the scalars and the flags are the operator's and are read
   // after the wait; every store comes after it.
-  T uv[4], wq[4], pv[4], sq[4], xv[4], rv[4], mv[4] = {T(1), T(1), T(1), T(1)};
-  if (tid < nvec) {
-    const long long t = o + 4 * tid;
-    ld4(p + t, pv);
-    ld4(sv + t, sq);
-    ld4(x + t, xv);
-    ld4(rvec + t, rv);
-    if (W) ld4(W + t, mv);
+  // Two groups of 4 entries per thread (v = tid and tid + stride): all of
+  // their operator-independent loads are issued before the wait, and the w
+  // loads of both after it, so that one resident wave covers the vectors
+  // with a single dependent round trip; groups beyond are handled by the
+  // loop after them.
+  constexpr int KG = 2;
+  T wq[KG][4], pv[KG][4], sq[KG][4], xv[KG][4], rv[KG][4], mv[KG][4];
+#pragma unroll
+  for (int g = 0; g < KG; ++g) {
+    const long long v = tid + g * stride;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) mv[g][k] = T(1);
+    if (v < nvec) {
+      const long long t = o + 4 * v;
+      ld4(p + t, pv[g]);
+      ld4(sv + t, sq[g]);
+      ld4(x + t, xv[g]);
+      ld4(rvec + t, rv[g]);
+      if (W) ld4(W + t, mv[g]);
+    }
   }
   grid_dep_wait();     // the operator launch before this one wrote w, the scalars and flags
   grid_dep_launch();   // the next operator launch may queue its blocks behind this wave
   if (flags[r]) return;
   const T zero[4] = {T(0), T(0), T(0), T(0)};
   T acc = T(0);
-  for (long long v = tid; v < nvec; v += stride) {
+  const T al = static_cast<T>(cg[r].alpha), be = static_cast<T>(cg[r].beta);
+#pragma unroll
+  for (int g = 0; g < KG; ++g) {
+    const long long v = tid + g * stride;
+    if (v < nvec) ld4(wv + o + 4 * v, wq[g]);
+  }
+  auto step = [&](long long v, T (&pg)[4], T (&sg)[4], T (&xg)[4], T (&rg)[4], const T (&mg)[4], const T (&wg)[4]) {
     const long long t = o + 4 * v;
-    if (v != tid) {
-      ld4(p + t, pv);
-      ld4(sv + t, sq);
-      ld4(x + t, xv);
-      ld4(rvec + t, rv);
-      if (W) ld4(W + t, mv);
-    }
-    ld4(wv + t, wq);
-    const T al = static_cast<T>(cg[r].alpha), be = static_cast<T>(cg[r].beta);
+    T ug[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      pv[k] = fma(be, pv[k], mv[k] * rv[k]);   // u = W r of this iteration, bitwise as stored
-      sq[k] = fma(be, sq[k], wq[k]);
-      xv[k] = fma(al, pv[k], xv[k]);
-      rv[k] = fma(-al, sq[k], rv[k]);
-      uv[k] = mv[k] * rv[k];
-      acc = fma(uv[k], rv[k], acc);
+      pg[k] = fma(be, pg[k], mg[k] * rg[k]);   // u = W r of this iteration, bitwise as stored
+      sg[k] = fma(be, sg[k], wg[k]);
+      xg[k] = fma(al, pg[k], xg[k]);
+      rg[k] = fma(-al, sg[k], rg[k]);
+      ug[k] = mg[k] * rg[k];
+      acc = fma(ug[k], rg[k], acc);
     }
-    st4(p + t, pv);
-    st4(sv + t, sq);
-    st4(x + t, xv);
-    st4(rvec + t, rv);
-    st4(u + t, uv);
+    st4(p + t, pg);
+    st4(sv + t, sg);
+    st4(x + t, xg);
+    st4(rvec + t, rg);
+    st4(u + t, ug);
     st4(wv + t, zero);
+  };
+#pragma unroll
+  for (int g = 0; g < KG; ++g) {
+    const long long v = tid + g * stride;
+    if (v < nvec) step(v, pv[g], sq[g], xv[g], rv[g], mv[g], wq[g]);
+  }
+  for (long long v = tid + KG * stride; v < nvec; v += stride) {
+    const long long t = o + 4 * v;
+    T p1[4], s1[4], x1[4], r1[4], m1[4] = {T(1), T(1), T(1), T(1)}, w1[4];
+    ld4(p + t, p1);
+    ld4(sv + t, s1);
+    ld4(x + t, x1);
+    ld4(rvec + t, r1);
+    if (W) ld4(W + t, m1);
+    ld4(wv + t, w1);
+    step(v, p1, s1, x1, r1, m1, w1);
   }
   {
     const T al = static_cast<T>(cg[r].alpha), be = static_cast<T>(cg[r].beta);
@@ -934,7 +960,8 @@ int cg_step_blocks(long long len) {
       per_sm = 1;
     cudaGetLastError();
   }
-  const long long need = (len / 4 + kVecThreads - 1) / kVecThreads;
+  // two groups of 4 entries per thread (cg_step_kernel)
+  const long long need = (len / 4 + 2 * kVecThreads - 1) / (2 * kVecThreads);
   return (int)std::max(1LL, std::min(need, (long long)sms * per_sm));
 }
 
