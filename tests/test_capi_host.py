@@ -71,6 +71,10 @@ def test_tuning_setters_reject_null_context(L):
     assert L.hdg_set_nodal_variant(None, 1) == 1
     assert L.hdg_set_operator_variant(None, 1) == 1
     assert L.hdg_set_dz_mode(None, 0) == 1
+    for v in (0, 1, 2, 3):
+        assert L.hdg_set_cg_variant(None, v) == 1
+    assert L.hdg_set_x1_segment(None, 2) == 1
+    assert L.hdg_set_slots_per_cta(None, 2) == 1
 
 
 def test_lowdim_setup_argument_errors(L):
