@@ -440,14 +440,12 @@ __global__ void cg_loop_cond(cudaGraphConditionalHandle h, const hdg::CgScalars*
   cudaGraphSetConditional(h, (any && t < cap) ? 1u : 0u);
 }
 
-// `count` CG iterations, two kernels each: the operator w = K-hat u with the
-// fused u^T w, then the single-reduction CG step (launch_cg_step).  Vectors:
-// x (d), r, u = W r, w (q), p, s = K-hat p.
-// `count` iterations of the fused CG step, one tile-kernel launch each
-// (tpt_tile.cuh, CgVecs): launch j applies the update of iteration j - 1 to
-// the face values it stages and applies the operator to u_j.  Buffers rotate
-// with j: r and s with period 2, w with period 3, so every sequence of
-// launches (eager or captured) starts at a multiple of kFusedPeriod.
+// `count` iterations of the fused CG step, one operator launch each (the
+// FP32 element-run kernel, tpt_fast.cuh, or the tile kernel, tpt_tile.cuh;
+// CgVecs): launch j applies the update of iteration j - 1 to the face values
+// it stages and applies the operator to u_j.  Buffers rotate with j: r and s
+// with period 2, w with period 3, so every sequence of launches (eager or
+// captured) starts at a multiple of kFusedPeriod.
 constexpr int kFusedPeriod = 6;
 template <typename T>
 hdg_status cg_fused_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* Wt, int count, cudaStream_t s) {
@@ -566,6 +564,9 @@ bool cg_persistent(hdg_ctx* c, int nrhs, const T* dinv, const T* Wt, cudaStream_
   return true;
 }
 
+// `count` CG iterations: the fused step, or two kernels each: the operator
+// w = K-hat u with the fused u^T w, then the single-reduction CG step
+// (launch_cg_step).  Vectors: x (d), r, u = W r, w (q), p, s = K-hat p.
 template <typename T>
 hdg_status cg_iterations(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, int count,
                          cudaStream_t s) {
@@ -754,10 +755,9 @@ hdg_status inner_cg(hdg_ctx* c, int nrhs, const double* lam, const double* rhat,
                     const double* scale = nullptr) {
   const long long T_ = c->ntrace;
   const long long tot = T_ * nrhs;
-  // the fused step (a mode of the tile kernel) where hdg_set_cg_variant asks
-  // for it and the tile kernel can run; else the two-kernel loop (operator,
-  // cg_step_kernel)
-  // (FP32: element runs or tiles; FP64: tiles only)
+  // the fused step (a mode of the operator kernels: FP32 element runs or
+  // tiles, FP64 tiles only) where hdg_set_cg_variant asks for it; else the
+  // two-kernel loop (operator, cg_step_kernel)
   c->fused_cg = (c->fused_enabled && c->op_variant != 3 && c->n <= hdg::kMaxSpecialisedN &&
                  !(sizeof(T) == 8 && c->op_variant == 1)) ? 1 : 0;
   for (int i : {W_R, W_D, W_P, W_Q, W_U, W_S}) HDG_TRY(ensure(c->ws[i], sizeof(T) * (size_t)tot));
