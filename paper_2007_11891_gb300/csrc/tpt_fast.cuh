@@ -62,17 +62,15 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   float* sm = reinterpret_cast<float*>(smem_raw);
 
   const int rhs = blockIdx.y;
-  // everything below reads what the previous kernel in the stream wrote
-  grid_dep_wait();
+  // Under programmatic dependent launch this grid may start while the
+  // previous kernel (the CG update) still runs.  The set-up below (indices,
+  // the first element's face offsets) reads nothing that kernel writes; the
+  // skip flags come from the operator launch before it, which completed
+  // before that kernel could let this one start.  Everything the previous
+  // kernel writes is read after grid_dep_wait().
   if (a.skip && a.skip[rhs]) return;   // uniform per block
   __shared__ CgScalars s_cg;
-  const HookPre hpre = hook_prefetch(a.hook, rhs, &s_cg);
   float al = 0.f, be = 0.f, gam = 0.f;
-  if constexpr (CG) {
-    __syncthreads();   // s_cg (hook_prefetch) visible to every thread
-    al = static_cast<float>(s_cg.alpha);
-    be = static_cast<float>(s_cg.beta);
-  }
 
   constexpr bool AL = fast_aligned(N);
   constexpr int SLOT_T = fast_slot_threads(N);
@@ -196,6 +194,14 @@ __global__ void __launch_bounds__(fast_max_threads(N), fast_min_ctas(N))
   FaceOffsets o = offsets(c1, c2, c3);
   float xlo1 = 0.f, xhi1 = 0.f, x2l = 0.f, x2h = 0.f, x3l = 0.f, x3h = 0.f;
   bool carried = false;   // fused step: x1 lo is the previous element's x1 hi
+
+  grid_dep_wait();   // from here on: data the previous kernel in the stream wrote
+  const HookPre hpre = hook_prefetch(a.hook, rhs, &s_cg);
+  if constexpr (CG) {
+    __syncthreads();   // s_cg (hook_prefetch) visible to every thread
+    al = static_cast<float>(s_cg.alpha);
+    be = static_cast<float>(s_cg.beta);
+  }
   if (e < eend) {
     if constexpr (CG) {
       fetch(o, c1, c2, c3, false);
