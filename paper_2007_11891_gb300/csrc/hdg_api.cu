@@ -108,7 +108,7 @@ struct hdg_ctx {
   int op_variant = 0;     // apply kernel: 0 automatic (use_tiles), 1 element runs, 2 element tiles, 3 runtime degree
   int nodal_variant = 0;  // FP64 nodal apply: 0 face-wise transforms + transformed kernel, 1 one kernel (HDG-TP)
   int dz_mode = 0;        // FP32 D_Z^-1 source: 0 automatic, 1 table, 2 in kernel
-  int fused_cg = 0;       // the current inner CG runs the fused tile-kernel step
+  int fused_cg = 0;       // the current inner CG runs the fused step
   int fused_enabled = 0;  // allow the fused step (hdg_set_cg_variant)
   int persist_enabled = 0;  // run the fused step as one persistent cooperative launch
 };
@@ -660,7 +660,7 @@ template <typename T>
 bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, cudaStream_t s,
                    hdg_status* st) {
   *st = HDG_OK;
-  const int kTrip = c->fused_cg ? kFusedPeriod : 4;
+  const int kTrip = c->fused_cg ? kFusedPeriod : 8;
   const long long per_iter = c->fused_cg ? 1 : 2;
   if (!c->loop_graphs_enabled || c->prof_on) return false;
   if (ensure(c->loopctl, sizeof(unsigned int) * 4) != HDG_OK) return false;
