@@ -660,7 +660,7 @@ template <typename T>
 bool cg_loop_graph(hdg_ctx* c, int nrhs, const T* dinv, const T* w, T* r, T* d, T* p, T* q, cudaStream_t s,
                    hdg_status* st) {
   *st = HDG_OK;
-  const int kTrip = c->fused_cg ? kFusedPeriod : 8;
+  const int kTrip = c->fused_cg ? kFusedPeriod : 16;
   const long long per_iter = c->fused_cg ? 1 : 2;
   if (!c->loop_graphs_enabled || c->prof_on) return false;
   if (ensure(c->loopctl, sizeof(unsigned int) * 4) != HDG_OK) return false;
