@@ -43,7 +43,7 @@ FP64_PEAK_TFLOPS_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12
 # DRAM bytes (read + write) per launch of the dominant kernel from one ncu
 # capture of the same kernel and workload (cold caches); None when the
 # kernel changed after the capture
-TRAFFIC_BYTES = {"op_fp32": 6827008}   # tpt_fast_kernel<9, 1, float, 0> in the CG loop: read 6.83 MB, write 0
+TRAFFIC_BYTES = {"op_fp32": 6820608}   # tpt_fast_kernel<9, 1, float, 0> in the CG loop: read 6.82 MB, write 0
 
 
 def peaks():
